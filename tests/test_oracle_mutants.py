@@ -1,0 +1,104 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake (a dropped term, a wrong sign, a wrong index, a
+swapped operand) in a private copy of the oracle's C source, compiles it, and
+runs the pin checks of ``test_oracle_pins`` against it: at least one pin has to
+fail.  The mistakes are planted in the oracle only, on the CPU.
+"""
+import contextlib
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "khydro_oracle.c")
+
+MUTANTS = {
+    "pvrs_sign": ("- 0.125 * (ur - ul)", "+ 0.125 * (ur - ul)"),
+    "dsl_sign": ("double dsl = -cl * ql;", "double dsl = cl * ql;"),
+    "sstar_num_swap": ("((pr - rr * ur * dsr) - (pl - rl * ul * dsl))", "((pl - rl * ul * dsl) - (pr - rr * ur * dsr))"),
+    "estar_term_dropped": ("(sstar - ul) * (sstar + pl / (rl * dsl))", "(sstar - ul) * sstar"),
+    "star_r_wrong_side": ("Us[2] = fac * wr[2];", "Us[2] = fac * wl[2];"),
+    "star_l_wrong_component": ("Us[2] = fac * wl[2];", "Us[2] = fac * wl[3];"),
+    "minmod_picks_larger": ("(fabs(a) < fabs(b)) ? a : b", "(fabs(a) < fabs(b)) ? b : a"),
+    "plm_half_dropped": ("wl[q] = s[1][q] + 0.5 * sl;", "wl[q] = s[1][q] + sl;"),
+    "plm_right_sign": ("wr[q] = s[2][q] - 0.5 * sr;", "wr[q] = s[2][q] + 0.5 * sr;"),
+    "reflect_no_negate": ("if (bc == ORC_BC_REFLECT) *vn = -*vn;", "if (bc == ORC_BC_REFLECT) *vn = *vn;"),
+    "periodic_off_by_one": ("src = side == 0 ? n - g : g - 1;", "src = side == 0 ? n - g : g;"),
+    "heun_no_average": ("U[q] = 0.5 * (U[q] + (U1[q] + dU[q]));", "U[q] = U1[q] + dU[q];"),
+    "dt_drops_velocity": ("double t = dx[d] / (fabs(w[1 + d]) + cs);", "double t = dx[d] / cs;"),
+    "energy_flux_no_p": ("F[4] = (E + p) * u;", "F[4] = E * u;"),
+    "momentum_flux_no_p": ("F[1] = mf * u + p;", "F[1] = mf * u;"),
+    "recover_ke_factor": ("double ke = 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);",
+                          "double ke = rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);"),
+    "transverse_slot": ("int t2 = d == 2 ? 1 : 2;", "int t2 = d == 2 ? 0 : 2;"),
+    "outflow_clamp_direction": ("if (side == 0) { if (*vn > 0.0) *vn = 0.0; }", "if (side == 0) { if (*vn < 0.0) *vn = 0.0; }"),
+    "q_no_sqrt": ("double ql = sqrt(1.0 + g1 * (ratl - 1.0));", "double ql = (1.0 + g1 * (ratl - 1.0));"),
+    "flux_diff_sign": ("dU[uc] = dU[uc] - dtdx * dif[0];", "dU[uc] = dU[uc] + dtdx * dif[0];"),
+    "two_shock_sign": ("pstar = (gl * pl + gr * pr - (ur - ul)) / (gl + gr);", "pstar = (gl * pl + gr * pr + (ur - ul)) / (gl + gr);"),
+    "sound_speed_gamma": ("double cl = sqrt(gamma * pl / rl);", "double cl = sqrt(pl / rl);"),
+    "prim_to_cons_energy": ("p / gm1 + 0.5 * rho * vsq", "p / gm1 + rho * vsq"),
+}
+
+# fast pins first; each entry is a zero-argument callable
+PIN_CHECKS = [
+    lambda: [pins.test_minmod_truth_table(a, b, w) for a, b, w in
+             [(1.0, 2.0, 1.0), (2.0, 1.0, 1.0), (-1.0, -3.0, -1.0), (1.0, -1.0, 0.0)]],
+    pins.test_hllc_consistency,
+    pins.test_hllc_stationary_contact_exact,
+    lambda: [pins.test_hllc_moving_contact_is_upwind(u) for u in (0.7, -0.7)],
+    pins.test_hllc_supersonic_upwinding,
+    pins.test_hllc_mirror_symmetry,
+    pins.test_uniform_dt_closed_form,
+    pins.test_prim_cons_roundtrip,
+    lambda: [pins.test_uniform_state_stays_uniform(nd) for nd in (1, 2, 3)],
+    lambda: [pins.test_conservation_periodic(nd) for nd in (1, 2, 3)],
+    pins.test_outflow_momentum_budget,
+    pins.test_reflecting_walls_conserve_mass_and_energy,
+    pins.test_outflow_does_not_inflow,
+    pins.test_implosion_diagonal_symmetry,
+    pins.test_sod_against_exact_solution,
+    lambda: pins.test_sound_wave_second_order(5.0 / 3.0, 1e-6),
+    pins.test_axis_interchange_identical,
+    lambda: [pins.test_axis_permutation_covariance(nd, pm) for nd, pm in
+             [(2, (1, 0)), (3, (1, 2, 0)), (3, (0, 2, 1))]],
+]
+
+
+@contextlib.contextmanager
+def mutated_oracle(find, repl):
+    src = open(SRC).read()
+    assert src.count(find) == 1, "mutation anchor must be unique: %r" % find
+    with tempfile.TemporaryDirectory() as td:
+        c = os.path.join(td, "mut.c")
+        so = os.path.join(td, "libmut.so")
+        open(c, "w").write(src.replace(find, repl))
+        subprocess.check_call(["gcc", "-O1", "-std=c99", "-ffp-contract=off", "-fopenmp", "-fPIC",
+                               "-shared", "-o", so, c, "-lm"])
+        saved_lib, saved_path = oracle._lib, oracle._LIB_PATH
+        oracle._lib = None
+        oracle._LIB_PATH = so
+        orig_build = oracle.build
+        oracle.build = lambda force=False: so
+        try:
+            yield
+        finally:
+            oracle._lib, oracle._LIB_PATH, oracle.build = saved_lib, saved_path, orig_build
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name):
+    find, repl = MUTANTS[name]
+    caught = None
+    with mutated_oracle(find, repl):
+        for check in PIN_CHECKS:
+            try:
+                check()
+            except (AssertionError, ValueError, FloatingPointError, ZeroDivisionError) as e:
+                caught = e
+                break
+    assert caught is not None, "mutant %s survived every pin" % name
