@@ -1,0 +1,295 @@
+"""Benchmark of the Godunov hydro step on GB300.
+
+Default workload: 3D periodic turbulence box 256^3 (rho = 1, p = 0.6,
+random-phase Gaussian velocity field with a k^-4 shell spectrum, rms Mach 1),
+mixed precision (FP32 reconstruction/HLLC, FP64 state), CFL 0.3.  One
+benchmark step = one Heun step of the whole grid = ncell cell-updates.
+The same grid is also timed on the all-FP64 path.
+
+Prints ONE JSON line.  ``--impl reference`` times the CPU oracle instead (the
+reference arm: a plain FP64 C program on the host cores).
+
+Multi-GPU: the path does not shard here (replicas only): each rank runs the
+same workload on its own GPU, the barrier and max-over-ranks timing are the
+only collectives, and ``value`` adds the ranks' cell-updates.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s (mixed vs FP64, 1 GB300, % HBM roofline); p99 solve latency"
+UNIT = "cell-updates/s"
+BYTES_PER_CELL_UPDATE_3D = 200  # stage 1: read Un, write U1; stage 2: read U1 and Un, write Un+1 (5 x 8 B each)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def cpu_oracle_rate(seconds: float = 10.0, n: int = 128):
+    """Oracle cell-updates/s on an n^3 turbulence box with all host cores."""
+    import oracle
+    from paper_2501_02317_gb300 import workloads as wl
+    cores = os.cpu_count() or 1
+    used = oracle.set_threads(cores)
+    mesh, W = wl.turbulence(n, prec=wl.PREC_FP64)
+    U = oracle.prim_to_cons(mesh, W)
+    t, steps, t0 = 0.0, 0, time.perf_counter()
+    while True:
+        U, t, _, _ = oracle.heun_step(mesh, U, t, 1e30)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return mesh.ncell * steps / el, used, "%d Heun steps of the %d^3 turbulence box (same recipe, seed 2)" % (steps, n)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2501_02317_gb300 import workloads as wl
+    cores = os.cpu_count() or 1
+    used = oracle.set_threads(cores)
+    n = 128
+    mesh, W = wl.turbulence(n, prec=wl.PREC_FP64)
+    U = oracle.prim_to_cons(mesh, W)
+    t = 0.0
+    for _ in range(args.warmup):
+        U, t, _, _ = oracle.heun_step(mesh, U, t, 1e30)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, t, _, _ = oracle.heun_step(mesh, U, t, 1e30)
+    el = time.perf_counter() - t0
+    value = mesh.ncell * args.steps / el
+    sample = "one oracle Heun step of a %d^3 turbulence box (same recipe as the 256^3 workload) per step" % n
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "turbulence-3d-%d^3-fp64-oracle" % n, "cells": mesh.ncell},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="side of the 3D turbulence box")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2501_02317_gb300 import build as kbuild
+    kbuild.build()
+    from paper_2501_02317_gb300 import khydro
+    from paper_2501_02317_gb300 import workloads as wl
+
+    peak_gbs, peak_kind = _peaks()
+    stream = torch.cuda.Stream()
+    mesh, W = wl.turbulence(args.n, prec=wl.PREC_MIXED)
+    ncell = mesh.ncell
+    K, Wm = args.steps, args.warmup
+    T_END = 1e30
+
+    def timed_steps(sim, k):
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.enqueue_steps(T_END, k)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+        return e0.elapsed_time(e1) / 1e3
+
+    # ---------------------------------------------------------- mixed (headline)
+    sim = khydro.Sim(mesh, stream=stream.cuda_stream)
+    sim.set_primitive(W)
+    sim.enqueue_steps(T_END, Wm)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        el = timed_steps(sim, K)
+    clocks = clk.summary()
+    el = max_over_ranks(el)
+    value = world * ncell * K / el
+    flags, floors = sim.flags()
+    ms = sim.profile_steps(T_END, 5)
+    stage_ms = ms[1] + ms[2]
+    achieved = BYTES_PER_CELL_UPDATE_3D * ncell / (stage_ms * 1e-3) / 1e9
+
+    # ---------------------------------------------------------- all-FP64 path
+    mesh64 = mesh.replace(prec=wl.PREC_FP64)
+    sim64 = khydro.Sim(mesh64, stream=stream.cuda_stream)
+    sim64.set_primitive(W)
+    sim64.enqueue_steps(T_END, 2)
+    torch.cuda.synchronize()
+    k64 = max(3, K // 10)
+    el64 = max_over_ranks(timed_steps(sim64, k64))
+    value64 = world * ncell * k64 / el64
+    ms64 = sim64.profile_steps(T_END, 2)
+    sim64.close()
+
+    # ---------------------------------------------------------- end to end (host buffers)
+    e2e = None
+    if not args.no_e2e:
+        Uh = torch.empty(mesh.shape, dtype=torch.float64, pin_memory=True).numpy()
+        sim.conserved(Uh)
+        ke = max(3, min(K, 10))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            sim.set_conserved(Uh)
+            sim.enqueue_steps(T_END, 1)
+            sim.conserved(Uh)
+        torch.cuda.synchronize()
+        el_e2e = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * ncell * ke / el_e2e, "unit": UNIT, "h2d_bytes_per_step": int(Uh.nbytes),
+               "d2h_bytes_per_step": int(Uh.nbytes), "steps": ke,
+               "api": "khy_set_conserved(host) + khy_enqueue_steps(1) + khy_get_conserved(host)"}
+    sim.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, cores, sample = cpu_oracle_rate()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+            "ms_per_step": 1e3 * el / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 state, f32 reconstruction/flux", "data": "synthetic",
+            "config": {"workload": "turbulence-3d-%d^3-mixed" % args.n, "cells": ncell, "prec": "mixed",
+                       "cfl": mesh.cfl, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2: two 5x8xN-byte states (%.0f MB each)" % (mesh.nvar * 8 * ncell / 1e6)},
+            "fp64": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": 1e3 * el64 / k64,
+                     "stage_ms": [ms64[1], ms64[2]]},
+            "mixed_over_fp64": value / value64,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                         "frac": achieved / peak_gbs, "traffic": None,
+                         "kernel": "stage_kernel (stage 1 + stage 2 of one Heun step)",
+                         "bytes_per_cell_update": BYTES_PER_CELL_UPDATE_3D, "stage_ms": [ms[1], ms[2]],
+                         "clock_ms": ms[0], "peak_kind": peak_kind},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": 3 * K,
+            "status_flags": flags, "floor_hits": floors,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

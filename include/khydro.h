@@ -1,0 +1,161 @@
+/*
+ * khydro.h -- C ABI of the GB300 Godunov hydrodynamics step library
+ * (libkhydro.so, sm_103a).
+ *
+ * The library advances the Euler equations (arXiv:2501.02317, Sec. 3, Eq. 2)
+ * on uniform Cartesian meshes in 1D, 2D and 3D with one explicit Godunov
+ * finite-volume scheme: conserved->primitive recovery and the CFL time step
+ * (Sec. 3.1), ghost zones from the physical boundary rules (Sec. 3.1.1),
+ * minmod-limited piecewise-linear reconstruction (Eq. 3, Sec. 3.2.2), the
+ * HLLC Riemann flux with the subtraction-safe wave speeds (Eq. 4, Eq. 5,
+ * Sec. 3.2.2) and the conservative update inside the Heun predictor-corrector
+ * (Sec. 3.3).  Two precisions: all-FP64, and mixed (FP32 reconstruction and
+ * Riemann flux, FP64 conserved state, recovery and flux-difference
+ * accumulation; Sec. 3.2.2).
+ *
+ * Conventions for every call:
+ *   - Every call returns a khy_status; nothing throws across the ABI.
+ *     khy_last_error() gives a thread-local message for the last failure.
+ *   - State arrays are field-major [nvar][nz][ny][nx], x fastest, float64,
+ *     interior cells only; nvar = 2 + ndim.  Conserved fields are
+ *     (rho, m_1..m_ndim, E); primitive fields are (rho, v_1..v_ndim, p).
+ *   - "count" arguments are element counts and must equal nvar * ncell,
+ *     otherwise KHY_ERR_ARG.
+ *   - Host pointers are owned by the caller and are only read or written
+ *     during the call.  Device pointers (the *_dev calls) must point to
+ *     device memory of the current CUDA device, 16-byte aligned.
+ *   - A khy_sim owns its device memory (allocated in khy_create, released in
+ *     khy_destroy) and runs on the CUDA stream given at creation (NULL = the
+ *     library creates a private non-blocking stream).  Calls on one khy_sim
+ *     must not overlap.
+ *   - Device-side anomalies (a non-positive density, a negative internal
+ *     energy or a NaN before the floors) latch in a device status word; the
+ *     next call that synchronises returns KHY_ERR_NONPHYSICAL.  Kernels never
+ *     trap.
+ */
+#ifndef KHYDRO_H
+#define KHYDRO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KHY_OK = 0,
+    KHY_ERR_ARG = -1,          /* invalid argument (sizes, enums, pointers) */
+    KHY_ERR_OOM = -2,          /* device allocation failed */
+    KHY_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    KHY_ERR_NONPHYSICAL = -4,  /* rho <= 0, E - ke < 0 or NaN seen by the recovery */
+    KHY_ERR_DT_UNDERFLOW = -5, /* the CFL step fell below 1e-300 or is not finite */
+    KHY_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
+    KHY_ERR_BUDGET = -7        /* serving: the job does not fit the HBM budget */
+} khy_status;
+
+typedef enum { KHY_PREC_FP64 = 0, KHY_PREC_MIXED = 1 } khy_prec;
+
+/* Physical boundary rules of Sec. 3.1.1 plus periodic wrap, per axis side. */
+typedef enum {
+    KHY_BC_PERIODIC = 0, /* wrap; must be set on both sides of an axis */
+    KHY_BC_OUTFLOW = 1,  /* copy the first interior cell, normal velocity clamped outward */
+    KHY_BC_FREE = 2,     /* copy the first interior cell */
+    KHY_BC_REFLECT = 3   /* mirror the interior, normal velocity negated */
+} khy_bc;
+
+/* Mesh and method parameters.  n[d] >= 2 for d < ndim and n[d] == 1 for
+ * d >= ndim; hi[d] > lo[d]; gamma > 1; 0 < cfl <= 1; floors >= 0. */
+typedef struct khy_mesh_desc {
+    int ndim;         /* 1, 2 or 3 */
+    int n[3];         /* interior cells per axis */
+    double lo[3];     /* domain lower corner */
+    double hi[3];     /* domain upper corner */
+    double gamma;     /* adiabatic index */
+    double cfl;       /* Courant number C of dt = C min dx_d / (|v_d| + c_s) */
+    int prec;         /* khy_prec */
+    int bc[3][2];     /* khy_bc per axis, [0] = low side, [1] = high side */
+    double rho_floor; /* floor on the recovered density (primitive only) */
+    double p_floor;   /* floor on the recovered pressure (primitive only) */
+} khy_mesh_desc;
+
+typedef struct khy_sim khy_sim;
+
+/* ------------------------------------------------------------ single grid */
+
+/* Validates *desc, allocates the state (U^n, U^1) and the device clock on the
+ * current CUDA device, and binds the stream (cudaStream_t, may be NULL).
+ * On success *out receives the simulation, time t = 0, state zero.
+ * Errors: KHY_ERR_ARG (invalid desc), KHY_ERR_OOM, KHY_ERR_CUDA. */
+khy_status khy_create(const khy_mesh_desc *desc, void *cuda_stream, khy_sim **out);
+
+/* Releases everything khy_create allocated.  NULL is ignored. */
+void khy_destroy(khy_sim *sim);
+
+/* Sets the boundary rule of one axis side (Sec. 3.1.1); axis < ndim,
+ * side 0 = low, 1 = high.  Periodic must end up on both sides of an axis or
+ * neither (checked at the next step).  Allowed between steps. */
+khy_status khy_set_boundary(khy_sim *sim, int axis, int side, int bc);
+
+/* Copies conserved U (host, count = nvar*ncell doubles) to the device state. */
+khy_status khy_set_conserved(khy_sim *sim, const double *U, size_t count);
+
+/* Copies primitive W (host) and converts it on the device to conserved
+ * variables: m_d = rho v_d, E = p/(gamma-1) + rho |v|^2/2 (Eq. 2). */
+khy_status khy_set_primitive(khy_sim *sim, const double *W, size_t count);
+
+/* Device-pointer variants: U_dev / W_dev is device memory with count doubles;
+ * the copy is stream-ordered on the simulation's stream (no host sync). */
+khy_status khy_set_conserved_dev(khy_sim *sim, const double *U_dev, size_t count);
+khy_status khy_set_primitive_dev(khy_sim *sim, const double *W_dev, size_t count);
+
+/* Sets the simulation time t. */
+khy_status khy_set_time(khy_sim *sim, double t);
+
+/* Advances by Heun steps (Sec. 3.3) until t reaches t_end or max_steps steps
+ * were taken (max_steps < 0: no limit).  Each step: dt = C min over cells and
+ * directions of dx_d/(|v_d| + c_s) from U^n (first sub-step only, Sec. 3.1),
+ * clipped so that the last step lands on t_end; U^1 = U^n + dt L(U^n);
+ * U^{n+1} = (U^n + (U^1 + dt L(U^1))) / 2.  The loop runs on the device in
+ * captured CUDA graphs; the host polls a device flag between graph chunks.
+ * steps_taken / t_out may be NULL.  Synchronises the stream. */
+khy_status khy_step_to(khy_sim *sim, double t_end, long max_steps, long *steps_taken, double *t_out);
+
+/* Enqueues exactly nsteps Heun steps toward t_end on the stream without any
+ * host synchronisation (steps past t_end are no-ops on the device).  Used for
+ * timing and for overlapping several simulations. */
+khy_status khy_enqueue_steps(khy_sim *sim, double t_end, long nsteps);
+
+/* Profiling: enqueues nsteps Heun steps toward t_end without graphs, with a
+ * CUDA event pair around each launch, synchronises, and writes the average
+ * duration in milliseconds of the clock launch (ms[0]), the stage-1 launch
+ * (ms[1]) and the stage-2 launch (ms[2]).  nsteps >= 1. */
+khy_status khy_profile_steps(khy_sim *sim, double t_end, long nsteps, float ms[3]);
+
+/* Copies the conserved state to host U (count doubles).  Synchronises. */
+khy_status khy_get_conserved(khy_sim *sim, double *U, size_t count);
+
+/* Stream-ordered copy of the conserved state to device memory U_dev. */
+khy_status khy_get_conserved_dev(khy_sim *sim, double *U_dev, size_t count);
+
+/* Current time, steps taken since creation and the last dt.  Synchronises. */
+khy_status khy_get_time(khy_sim *sim, double *t, long *steps, double *last_dt);
+
+/* Conservation totals (diagnostic): Neumaier-compensated sum of every
+ * conserved field over the interior cells, out[0..nvar-1].  Synchronises. */
+khy_status khy_totals(khy_sim *sim, double out[5]);
+
+/* Latched device status bits (1 = non-physical state seen, 2 = a floor was
+ * applied) and the number of floor applications; clears them when clear != 0. */
+khy_status khy_get_flags(khy_sim *sim, unsigned *flags, unsigned long long *floor_hits, int clear);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *khy_last_error(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int khy_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KHYDRO_H */

@@ -1,0 +1,18 @@
+// khy_fp64.cu -- all-FP64 instantiation of the hydro kernels.  Built with
+// -fmad=false: every double operation rounds on its own, in the order the
+// CPU reference uses, so results match it bit for bit.
+#include "khy_launch.cuh"
+
+namespace khy {
+
+cudaError_t launch_stage_fp64(const StageArgs &a, int stage, cudaStream_t s) {
+    return launch_stage_prec<double>(a, stage, s);
+}
+
+cudaError_t launch_dt_fp64(const Geom &g, const double *U, Clock *clk, cudaStream_t s) {
+    return launch_dt_any(g, U, clk, s);
+}
+
+cudaError_t prepare_fp64(int ndim) { return prepare_prec<double>(ndim); }
+
+}  // namespace khy

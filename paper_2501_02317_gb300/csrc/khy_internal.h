@@ -1,0 +1,27 @@
+// khy_internal.h -- launchers shared between the translation units of
+// libkhydro.so (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "khy_kernels.cuh"
+
+namespace khy {
+
+// Stage kernel (stage = 1 or 2) and CFL-minimum kernel for each precision.
+// khy_fp64.cu builds the double instantiations with -fmad=false; khy_mixed.cu
+// builds the float (mixed) instantiations.
+cudaError_t launch_stage_fp64(const StageArgs &a, int stage, cudaStream_t s);
+cudaError_t launch_dt_fp64(const Geom &g, const double *U, Clock *clk, cudaStream_t s);
+cudaError_t launch_stage_mixed(const StageArgs &a, int stage, cudaStream_t s);
+cudaError_t launch_dt_mixed(const Geom &g, const double *U, Clock *clk, cudaStream_t s);
+
+// Sets the shared-memory limits of the stage kernels of one dimensionality;
+// call before the first launch (in particular before a stream capture).
+cudaError_t prepare_fp64(int ndim);
+cudaError_t prepare_mixed(int ndim);
+
+// Chunk length along the march axis used for a grid (planes per CTA).
+int march_chunk(const Geom &g);
+
+}  // namespace khy

@@ -1,0 +1,18 @@
+// khy_mixed.cu -- mixed-precision instantiation of the hydro kernels
+// (Sec. 3.2.2): PLM reconstruction and the HLLC flux in FP32; conserved state,
+// primitive recovery and flux-difference accumulation in FP64.
+#include "khy_launch.cuh"
+
+namespace khy {
+
+cudaError_t launch_stage_mixed(const StageArgs &a, int stage, cudaStream_t s) {
+    return launch_stage_prec<float>(a, stage, s);
+}
+
+cudaError_t launch_dt_mixed(const Geom &g, const double *U, Clock *clk, cudaStream_t s) {
+    return launch_dt_any(g, U, clk, s);
+}
+
+cudaError_t prepare_mixed(int ndim) { return prepare_prec<float>(ndim); }
+
+}  // namespace khy

@@ -1,0 +1,39 @@
+"""Shared helpers of the tests (no method arithmetic beyond diagnostics)."""
+import numpy as np
+
+import oracle
+
+
+def rel_l1(a, b):
+    """Sum |a - b| / sum |b| (b is the reference)."""
+    den = float(np.abs(b).sum())
+    return float(np.abs(a - b).sum()) / den if den > 0 else float(np.abs(a - b).sum())
+
+
+def pressure_np(mesh, U):
+    """Pressure of a conserved state, plain numpy (diagnostic only)."""
+    rho = U[0]
+    ke = 0.5 * sum(U[1 + d] ** 2 for d in range(mesh.ndim)) / rho
+    return (mesh.gamma - 1.0) * (U[mesh.nvar - 1] - ke)
+
+
+def oracle_run(mesh, W, t_end=1e30, max_steps=1 << 40):
+    U0 = oracle.prim_to_cons(mesh, W)
+    U, t, s, f = oracle.run(mesh, U0, 0.0, t_end, max_steps)
+    return U, t, s, f
+
+
+def gpu_run(mesh, W, t_end=1e30, max_steps=-1):
+    from paper_2501_02317_gb300 import khydro
+    with khydro.Sim(mesh) as sim:
+        sim.set_primitive(np.ascontiguousarray(W))
+        s, t = sim.step_to(t_end, max_steps)
+        U = sim.conserved()
+        _, _, dt = sim.time()
+    return U, t, s, dt
+
+
+def field_errors(mesh, U, Uref):
+    errs = [rel_l1(U[q], Uref[q]) for q in range(mesh.nvar)]
+    errs.append(rel_l1(pressure_np(mesh, U), pressure_np(mesh, Uref)))
+    return errs

@@ -1,0 +1,265 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Gates (the accuracy targets of the method's mixed-precision scheme):
+  * all-FP64 GPU path vs oracle: relative L1 <= 1e-12 per conserved field
+    (the FP64 kernels evaluate the oracle's operation order without FMA
+    contraction, so in practice the two agree to the last bit)
+  * mixed path (FP32 reconstruction/flux, FP64 state) vs oracle: relative L1
+    <= 1e-5 in density and <= 1e-4 in pressure
+  * conserved totals drift <= 1e-14 relative per step with periodic boundaries
+"""
+import numpy as np
+import pytest
+
+import oracle
+from hydro_util import field_errors, gpu_run, oracle_run, pressure_np, rel_l1
+from paper_2501_02317_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_RHO_TOL = 1e-5
+MIXED_P_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2501_02317_gb300 import build as kbuild
+    from paper_2501_02317_gb300 import khydro
+    kbuild.build()
+    khydro.lib()
+    oracle.set_threads(0)
+
+
+def check(mesh, U, Uref, prec):
+    errs = field_errors(mesh, U, Uref)
+    if prec == wl.PREC_FP64:
+        assert max(errs) <= FP64_TOL, errs
+    else:
+        assert errs[0] <= MIXED_RHO_TOL and errs[-1] <= MIXED_P_TOL, errs
+    return errs
+
+
+# ------------------------------------------------------------ 1D Sod
+
+@pytest.mark.parametrize("prec", [wl.PREC_FP64, wl.PREC_MIXED])
+def test_sod_512_full_run(prec):
+    mesh, W = wl.sod(512, prec=prec)
+    Uo, to, so, fo = oracle_run(mesh, W, 0.2)
+    U, t, s, dt = gpu_run(mesh, W, 0.2)
+    assert t == 0.2 and to == 0.2
+    if prec == wl.PREC_FP64:
+        assert s == so
+        np.testing.assert_array_equal(U, Uo)   # bitwise
+    check(mesh, U, Uo, prec)
+
+
+# ------------------------------------------------------------ 2D / 3D, tiles and ragged tails
+
+CASES_2D = [(64, 64), (130, 70), (257, 33), (5, 9), (2, 2)]
+CASES_3D = [(32, 16, 40), (37, 11, 9), (2, 3, 2), (66, 10, 35)]
+
+
+@pytest.mark.parametrize("prec", [wl.PREC_FP64, wl.PREC_MIXED])
+@pytest.mark.parametrize("n", CASES_2D)
+def test_2d_random_state_periodic(prec, n):
+    mesh = wl.Mesh(ndim=2, n=(n[0], n[1], 1), gamma=1.4, cfl=0.4, prec=prec)
+    W = wl.random_jumpy(mesh, seed=n[0] * 7 + n[1])
+    Uo, to, so, _ = oracle_run(mesh, W, max_steps=6)
+    U, t, s, _ = gpu_run(mesh, W, max_steps=6)
+    assert s == so == 6
+    if prec == wl.PREC_FP64:
+        np.testing.assert_array_equal(U, Uo)
+    check(mesh, U, Uo, prec)
+
+
+@pytest.mark.parametrize("prec", [wl.PREC_FP64, wl.PREC_MIXED])
+@pytest.mark.parametrize("n", CASES_3D)
+def test_3d_random_state_periodic(prec, n):
+    mesh = wl.Mesh(ndim=3, n=n, gamma=5.0 / 3.0, cfl=0.3, prec=prec)
+    W = wl.random_jumpy(mesh, seed=sum(n))
+    Uo, to, so, _ = oracle_run(mesh, W, max_steps=4)
+    U, t, s, _ = gpu_run(mesh, W, max_steps=4)
+    assert s == so == 4
+    if prec == wl.PREC_FP64:
+        np.testing.assert_array_equal(U, Uo)
+    check(mesh, U, Uo, prec)
+
+
+BCS = [
+    ((wl.BC_OUTFLOW, wl.BC_REFLECT), (wl.BC_FREE, wl.BC_OUTFLOW), (wl.BC_REFLECT, wl.BC_FREE)),
+    ((wl.BC_REFLECT, wl.BC_REFLECT), (wl.BC_PERIODIC, wl.BC_PERIODIC), (wl.BC_OUTFLOW, wl.BC_OUTFLOW)),
+]
+
+
+@pytest.mark.parametrize("prec", [wl.PREC_FP64, wl.PREC_MIXED])
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_boundaries(prec, bc, ndim):
+    n = {1: (67, 1, 1), 2: (45, 38, 1), 3: (21, 14, 17)}[ndim]
+    mesh = wl.Mesh(ndim=ndim, n=n, gamma=1.4, cfl=0.3, prec=prec, bc=bc)
+    W = wl.random_smooth(mesh, seed=ndim)
+    # flows toward and away from every wall
+    Uo, to, so, _ = oracle_run(mesh, W, max_steps=8)
+    U, t, s, _ = gpu_run(mesh, W, max_steps=8)
+    assert s == so
+    if prec == wl.PREC_FP64:
+        np.testing.assert_array_equal(U, Uo)
+    check(mesh, U, Uo, prec)
+
+
+# ------------------------------------------------------------ workloads of the configs
+
+@pytest.mark.parametrize("prec", [wl.PREC_FP64, wl.PREC_MIXED])
+def test_kelvin_helmholtz_128_to_t(prec):
+    mesh, W = wl.kelvin_helmholtz(128, prec=prec)
+    Uo, to, so, _ = oracle_run(mesh, W, 0.2)
+    U, t, s, _ = gpu_run(mesh, W, 0.2)
+    assert t == to == 0.2
+    check(mesh, U, Uo, prec)
+
+
+@pytest.mark.parametrize("prec", [wl.PREC_FP64, wl.PREC_MIXED])
+def test_turbulence_48_steps(prec):
+    mesh, W = wl.turbulence(48, prec=prec)
+    Uo, to, so, _ = oracle_run(mesh, W, max_steps=20)
+    U, t, s, _ = gpu_run(mesh, W, max_steps=20)
+    assert s == so == 20
+    check(mesh, U, Uo, prec)
+
+
+@pytest.mark.parametrize("prec", [wl.PREC_FP64, wl.PREC_MIXED])
+def test_implosion_reflecting(prec):
+    mesh, W = wl.liska_wendroff(64, prec=prec)
+    Uo, to, so, _ = oracle_run(mesh, W, max_steps=40)
+    U, t, s, _ = gpu_run(mesh, W, max_steps=40)
+    check(mesh, U, Uo, prec)
+    if prec == wl.PREC_FP64:
+        # diagonal symmetry to the last bit (Sec. 4.4)
+        np.testing.assert_array_equal(U[0, 0], U[0, 0].T)
+
+
+# ------------------------------------------------------------ full sizes
+
+@pytest.mark.parametrize("prec", [wl.PREC_FP64, wl.PREC_MIXED])
+def test_kelvin_helmholtz_1024_full_size(prec):
+    mesh, W = wl.kelvin_helmholtz(1024, prec=prec)
+    Uo, to, so, _ = oracle_run(mesh, W, max_steps=3)
+    U, t, s, _ = gpu_run(mesh, W, max_steps=3)
+    assert s == 3
+    check(mesh, U, Uo, prec)
+
+
+@pytest.mark.parametrize("prec", [wl.PREC_MIXED, wl.PREC_FP64])
+def test_turbulence_256_full_size(prec):
+    mesh, W = wl.turbulence(256, prec=prec)
+    Uo, to, so, _ = oracle_run(mesh, W, max_steps=2)
+    U, t, s, _ = gpu_run(mesh, W, max_steps=2)
+    assert s == 2
+    check(mesh, U, Uo, prec)
+
+
+# ------------------------------------------------------------ properties
+
+@pytest.mark.parametrize("prec", [wl.PREC_FP64, wl.PREC_MIXED])
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_conservation_per_step(prec, ndim):
+    from paper_2501_02317_gb300 import khydro
+    n = {1: (300, 1, 1), 2: (96, 80, 1), 3: (40, 24, 36)}[ndim]
+    mesh = wl.Mesh(ndim=ndim, n=n, gamma=5.0 / 3.0, cfl=0.3, prec=prec)
+    W = wl.random_jumpy(mesh, seed=4)
+    with khydro.Sim(mesh) as sim:
+        sim.set_primitive(W)
+        prev = sim.totals()
+        scale = np.abs(sim.conserved()).reshape(mesh.nvar, -1).sum(axis=1)
+        for _ in range(10):
+            sim.step_to(1e30, 1)
+            cur = sim.totals()
+            assert np.all(np.abs(cur - prev) / scale <= 1e-14), (cur - prev) / scale
+            prev = cur
+            scale = np.abs(sim.conserved()).reshape(mesh.nvar, -1).sum(axis=1)
+
+
+def test_axis_interchange_bitwise():
+    # Sec. 4.2: the same tube along x, y or z gives identical results
+    m1, W1 = wl.sod(96, axis=0, ndim=1)
+    U1, t1, s1, _ = gpu_run(m1, W1, 0.2)
+    for ndim, axis in [(2, 1), (2, 0), (3, 2), (3, 1), (3, 0)]:
+        m, W = wl.sod(96, axis=axis, ndim=ndim, ntrans=5)
+        U, t, s, _ = gpu_run(m, W, 0.2)
+        assert s == s1
+        rho = np.moveaxis(U[0], 2 - axis, -1).reshape(-1, 96)
+        for row in rho:
+            np.testing.assert_array_equal(row, U1[0].ravel())
+
+
+def test_uniform_state_stays_uniform():
+    for prec in (wl.PREC_FP64, wl.PREC_MIXED):
+        m = wl.Mesh(ndim=3, n=(20, 9, 7), gamma=5.0 / 3.0, cfl=0.3, prec=prec)
+        W = wl.uniform(m)
+        U0 = oracle.prim_to_cons(m, W)
+        U, t, s, _ = gpu_run(m, W, max_steps=12)
+        np.testing.assert_array_equal(U, U0)
+
+
+def test_set_primitive_matches_oracle_conversion():
+    from paper_2501_02317_gb300 import khydro
+    m = wl.Mesh(ndim=3, n=(9, 8, 7))
+    W = wl.random_jumpy(m)
+    with khydro.Sim(m) as sim:
+        sim.set_primitive(W)
+        np.testing.assert_array_equal(sim.conserved(), oracle.prim_to_cons(m, W))
+
+
+def test_split_run_equals_straight_run():
+    # checkpoint/resume: U and t are the whole state of the method
+    from paper_2501_02317_gb300 import khydro
+    mesh, W = wl.kelvin_helmholtz(96, prec=wl.PREC_MIXED)
+    Ua, ta, sa, _ = gpu_run(mesh, W, 0.1)
+    with khydro.Sim(mesh) as sim:
+        sim.set_primitive(W)
+        sim.step_to(0.04)
+        Umid = sim.conserved()
+        tmid, _, _ = sim.time()
+    with khydro.Sim(mesh) as sim2:
+        sim2.set_conserved(Umid)
+        sim2.set_time(tmid)
+        sim2.step_to(0.1)
+        Ub = sim2.conserved()
+    np.testing.assert_array_equal(Ua, Ub)
+
+
+def test_step_to_lands_on_t_end_and_respects_max_steps():
+    from paper_2501_02317_gb300 import khydro
+    mesh, W = wl.sod(128)
+    with khydro.Sim(mesh) as sim:
+        sim.set_primitive(W)
+        s, t = sim.step_to(0.05, 3)
+        assert s == 3 and t < 0.05
+        s, t = sim.step_to(0.05)
+        assert t == 0.05
+        s2, t2 = sim.step_to(0.05)
+        assert s2 == 0 and t2 == 0.05
+
+
+def test_nonphysical_state_is_reported():
+    from paper_2501_02317_gb300 import khydro
+    mesh = wl.Mesh(ndim=1, n=(64, 1, 1))
+    W = wl.uniform(mesh)
+    U = oracle.prim_to_cons(mesh, W)
+    U[2, 0, 0, 10] = -1.0  # negative total energy in one cell
+    with khydro.Sim(mesh) as sim:
+        sim.set_conserved(U)
+        with pytest.raises(khydro.KhydroError) as ei:
+            sim.step_to(1.0, 1)
+        assert ei.value.status == -4
+        flags, _ = sim.flags(clear=True)
+        assert flags & 1
+
+
+def test_dt_matches_oracle():
+    mesh, W = wl.kelvin_helmholtz(80, prec=wl.PREC_FP64)
+    U0 = oracle.prim_to_cons(mesh, W)
+    _, _, dt_o, _ = oracle.heun_step(mesh, U0, 0.0, 1.0)
+    _, t, s, dt = gpu_run(mesh, W, max_steps=1)
+    assert dt == dt_o and t == dt_o
