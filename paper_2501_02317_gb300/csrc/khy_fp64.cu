@@ -10,7 +10,7 @@ cudaError_t launch_stage_fp64(const StageArgs &a, int stage, cudaStream_t s) {
 }
 
 cudaError_t launch_dt_fp64(const Geom &g, const double *U, Clock *clk, cudaStream_t s) {
-    return launch_dt_any(g, U, clk, s);
+    return launch_dt_prec<double>(g, U, clk, s);
 }
 
 cudaError_t prepare_fp64(int ndim) { return prepare_prec<double>(ndim); }

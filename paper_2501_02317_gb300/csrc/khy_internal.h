@@ -4,7 +4,7 @@
 
 #include <cuda_runtime.h>
 
-#include "khy_kernels.cuh"
+#include "khy_stage.cuh"
 
 namespace khy {
 
@@ -16,12 +16,10 @@ cudaError_t launch_dt_fp64(const Geom &g, const double *U, Clock *clk, cudaStrea
 cudaError_t launch_stage_mixed(const StageArgs &a, int stage, cudaStream_t s);
 cudaError_t launch_dt_mixed(const Geom &g, const double *U, Clock *clk, cudaStream_t s);
 
-// Sets the shared-memory limits of the stage kernels of one dimensionality;
-// call before the first launch (in particular before a stream capture).
+// Sets the shared-memory limits of the stage kernels of one dimensionality
+// and caches their persistent grid sizes; call before the first launch (in
+// particular before a stream capture).
 cudaError_t prepare_fp64(int ndim);
 cudaError_t prepare_mixed(int ndim);
-
-// Chunk length along the march axis used for a grid (planes per CTA).
-int march_chunk(const Geom &g);
 
 }  // namespace khy

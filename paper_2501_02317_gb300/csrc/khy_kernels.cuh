@@ -1,35 +1,12 @@
-// khy_kernels.cuh -- device code of the Godunov hydro step (sm_103a).
+// khy_kernels.cuh -- device building blocks of the Godunov hydro step
+// (sm_103a): geometry and clock records, the ghost-zone index map
+// (Sec. 3.1.1), the FP64 primitive recovery and CFL candidate (Sec. 3.1), the
+// minmod limiter (Eq. 3), the HLLC flux (Eq. 4, Eq. 5) and the PLM face flux
+// (Sec. 3.2.2).  The stage kernel that puts them together is khy_stage.cuh.
 //
-// One Heun step (Sec. 3.3) is three launches on one stream:
-//   clock_kernel    : dt = C * min dx_d/(|v_d|+c_s) from the minimum that the
-//                     previous stage-2 launch (or dt_kernel) accumulated; dt is
-//                     clipped to t_end; t and the step counter advance.
-//   stage_kernel<1> : U1 = Un + dt L(Un)
-//   stage_kernel<2> : Un+1 = (Un + (U1 + dt L(U1))) / 2, written over Un, and
-//                     the CFL minimum of Un+1 for the next step (Sec. 3.1: the
-//                     step length is computed during the variable conversion).
-//
-// The stage kernel fuses the whole spatial operator: each CTA owns a tile of
-// columns along the slowest ("march") axis -- z in 3D, y in 2D -- and walks
-// it plane by plane.  Each plane of the conserved state, with two halo cells
-// on every side, is loaded once, converted to primitives (Sec. 3.1) with the
-// ghost-zone rules applied by index mapping (Sec. 3.1.1), and kept in a
-// four-plane ring in shared memory (the row staging of Sec. 3.2.1, extended
-// to a 2.5D march).  In-plane face fluxes are computed as a flat task list
-// over the CTA's threads; the face along the march axis is computed by the
-// thread that owns the column.  Each face flux is computed once per CTA and
-// used with + on one cell and - on the other; faces on a tile edge are
-// recomputed by the neighbouring CTA from the same inputs by the same code,
-// so both sides see the identical value.
-//
-// Precision (Sec. 3.2.2): template parameter R is the reconstruction/Riemann
-// type: double for the all-FP64 path, float for the mixed path.  The
-// conserved state, the primitive recovery and the flux-difference
-// accumulation are always FP64.
-//
-// The FP64 instantiation is compiled with -fmad=false and evaluates every
-// floating-point operation in the same order as the CPU reference, so the
-// two agree to the last bit.
+// Everything here evaluates floating-point operations in the same order as
+// the CPU reference.  In the FP64 translation unit (built with -fmad=false)
+// that makes the two agree to the last bit.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -261,275 +238,6 @@ __device__ __forceinline__ void face_flux(const R (&s)[4][ND + 2], int dir, cons
     hllc<R, NT>(k, wl, wr, Fr);
 #pragma unroll
     for (int j = 0; j < ND + 2; ++j) F[slot[j]] = Fr[j];
-}
-
-// ---------------------------------------------------------- kernels
-
-struct StageArgs {
-    Geom g;
-    const double *Uin;    // state the fluxes are computed from (Un or U1)
-    const double *Ubase;  // Un (stage 2 average); unused in stage 1
-    double *Uout;         // U1 (stage 1) or Un+1 (stage 2, may alias Ubase)
-    Clock *clk;
-    int kchunk;           // planes per CTA along the march axis
-};
-
-template <int ND, int TX, int TY>
-struct Tile {
-    static constexpr int NV = ND + 2;
-    static constexpr int PX = TX + 4;
-    static constexpr int PY = (ND == 3) ? TY + 4 : 1;
-    static constexpr int PC = PX * PY;
-    static constexpr int NSLOT = (ND == 1) ? 1 : 4;
-    static constexpr int NT = TX * TY;
-    static constexpr int NXF = (TX + 1) * TY;
-    static constexpr int NYF = (ND == 3) ? TX * (TY + 1) : 0;
-    template <class R>
-    static constexpr size_t smem_bytes() {
-        return sizeof(R) * ((size_t)NSLOT * NV * PC + (size_t)NV * NXF + (size_t)NV * NYF);
-    }
-};
-
-template <int ND, class R, int STAGE, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) stage_kernel(StageArgs a) {
-    using T = Tile<ND, TX, TY>;
-    constexpr int NV = T::NV, PX = T::PX, PC = T::PC, NT = T::NT;
-    constexpr int DM = ND - 1;  // march axis for ND >= 2
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *sW = reinterpret_cast<R *>(smem_raw);          // [NSLOT][NV][PC]
-    R *sFx = sW + (size_t)T::NSLOT * NV * PC;         // [NV][TY][TX+1]
-    R *sFy = sFx + (size_t)NV * T::NXF;               // [NV][TY+1][TX]
-
-    const Geom &g = a.g;
-    const Clock *clk = a.clk;
-    if (!clk->active) return;
-    double dtdx[3] = {clk->dtdx[0], clk->dtdx[1], clk->dtdx[2]};
-    const Consts<R> kc = make_consts<R>(g);
-    const long long N = g.ncell;
-
-    const int tid = threadIdx.x;
-    const int tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX;
-    const int y0 = (ND == 3) ? blockIdx.y * TY : 0;
-    const int chunk = (ND == 3) ? blockIdx.z : (ND == 2 ? blockIdx.y : 0);
-    const int nm = (ND >= 2) ? g.n[DM] : 1;
-    const int k0 = chunk * a.kchunk;
-    const int k1 = min(k0 + a.kchunk, nm);
-
-    unsigned flags = 0, floors = 0;
-    double wmin = __longlong_as_double((long long)kInfBits);
-
-    // load plane L (march coordinate; ignored in 1D) into ring slot
-    auto load_plane = [&](int L, int slot) {
-        R *dst = sW + (size_t)slot * NV * PC;
-        for (int e = tid; e < PC; e += NT) {
-            const int hx = e % PX, hy = e / PX;
-            int act[3] = {0, 0, 0};
-            int c[3] = {0, 0, 0};
-            c[0] = bc_map(x0 - 2 + hx, g.n[0], g.bc[0][0], g.bc[0][1], &act[0]);
-            if (ND == 3) {
-                c[1] = bc_map(y0 - 2 + hy, g.n[1], g.bc[1][0], g.bc[1][1], &act[1]);
-                c[2] = bc_map(L, g.n[2], g.bc[2][0], g.bc[2][1], &act[2]);
-            } else if (ND == 2) {
-                c[1] = bc_map(L, g.n[1], g.bc[1][0], g.bc[1][1], &act[1]);
-            }
-            const long long idx = ((long long)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
-            double u[NV], w[NV];
-#pragma unroll
-            for (int q = 0; q < NV; ++q) u[q] = __ldg(a.Uin + (long long)q * N + idx);
-            unsigned fl = 0;
-            recover<ND>(u, g, w, flags, fl);
-            const bool interior = hx >= 2 && hx < TX + 2 && x0 - 2 + hx < g.n[0] &&
-                                  (ND != 3 || (hy >= 2 && hy < TY + 2 && y0 - 2 + hy < g.n[1])) &&
-                                  (ND == 1 || (L >= k0 && L < k1));
-            if (interior) floors += fl;
-#pragma unroll
-            for (int d = 0; d < ND; ++d) w[1 + d] = apply_vrule(w[1 + d], act[d]);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) dst[(size_t)q * PC + e] = (R)w[q];
-        }
-    };
-
-    // stencil gather along direction dir from a ring slot
-    auto gather = [&](const R *base, int e0, int stride, R (&s)[4][NV]) {
-#pragma unroll
-        for (int o = 0; o < 4; ++o)
-#pragma unroll
-            for (int q = 0; q < NV; ++q) s[o][q] = base[(size_t)q * PC + e0 + o * stride];
-    };
-
-    // in-plane face fluxes of the plane in ring slot `slot` into sFx / sFy
-    auto inplane_faces = [&](int slot) {
-        const R *pl = sW + (size_t)slot * NV * PC;
-        for (int f = tid; f < T::NXF + T::NYF; f += NT) {
-            R s[4][NV], F[NV];
-            if (f < T::NXF) {
-                const int fx = f % (TX + 1), fy = f / (TX + 1);
-                const int hy = (ND == 3) ? fy + 2 : 0;
-                gather(pl, hy * PX + fx, 1, s);
-                face_flux<ND, R>(s, 0, kc, F);
-#pragma unroll
-                for (int q = 0; q < NV; ++q) sFx[(size_t)q * T::NXF + f] = F[q];
-            } else {
-                const int f2 = f - T::NXF;
-                const int fxx = f2 % TX, fyy = f2 / TX;
-                gather(pl, fyy * PX + fxx + 2, PX, s);
-                face_flux<ND, R>(s, 1, kc, F);
-#pragma unroll
-                for (int q = 0; q < NV; ++q) sFy[(size_t)q * T::NYF + f2] = F[q];
-            }
-        }
-    };
-
-    // update of the cell (tx, ty) of plane `cur` given the march-face fluxes
-    auto update_cell = [&](int cur, const R (&Fmlo)[NV], const R (&Fmhi)[NV]) {
-        const int gx = x0 + tx;
-        const int gy = (ND == 3) ? y0 + ty : (ND == 2 ? cur : 0);
-        const int gz = (ND == 3) ? cur : 0;
-        if (gx >= g.n[0] || (ND == 3 && gy >= g.n[1])) return;
-        const long long idx = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
-        double acc[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            const R *fx = sFx + (size_t)q * T::NXF + ty * (TX + 1) + tx;
-            acc[q] = 0.0 - dtdx[0] * ((double)fx[1] - (double)fx[0]);
-        }
-        if (ND == 3) {
-#pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                const R *fy = sFy + (size_t)q * T::NYF + ty * TX + tx;
-                acc[q] = acc[q] - dtdx[1] * ((double)fy[TX] - (double)fy[0]);
-            }
-        }
-        if (ND >= 2) {
-#pragma unroll
-            for (int q = 0; q < NV; ++q) acc[q] = acc[q] - dtdx[DM] * ((double)Fmhi[q] - (double)Fmlo[q]);
-        }
-        double un[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            const double u = a.Uin[(long long)q * N + idx];
-            double r;
-            if (STAGE == 1) r = u + acc[q];
-            else r = 0.5 * (a.Ubase[(long long)q * N + idx] + (u + acc[q]));
-            un[q] = r;
-            a.Uout[(long long)q * N + idx] = r;
-        }
-        if (STAGE == 2) {
-            double w[NV];
-            unsigned fl = 0;
-            recover<ND>(un, g, w, flags, fl);
-            const double c = cfl_candidate<ND>(w, g);
-            if (c < wmin) wmin = c;
-        }
-    };
-
-    if (ND == 1) {
-        load_plane(0, 0);
-        __syncthreads();
-        inplane_faces(0);
-        __syncthreads();
-        R dummy[NV];
-        update_cell(0, dummy, dummy);
-    } else {
-        R Fmlo[NV], Fmhi[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) { Fmlo[q] = R(0); Fmhi[q] = R(0); }
-        for (int L = k0 - 2; L <= k1 + 1; ++L) {
-            load_plane(L, L & 3);
-            __syncthreads();
-            if (L >= k0 + 1) {
-                const int cur = L - 2;
-                // march face between cur and cur+1 from planes cur-1 .. cur+2
-                {
-                    R s[4][NV];
-                    const int e = (ND == 3) ? (ty + 2) * PX + tx + 2 : tx + 2;
-#pragma unroll
-                    for (int o = 0; o < 4; ++o) {
-                        const R *pl = sW + (size_t)((cur - 1 + o) & 3) * NV * PC;
-#pragma unroll
-                        for (int q = 0; q < NV; ++q) s[o][q] = pl[(size_t)q * PC + e];
-                    }
-                    face_flux<ND, R>(s, DM, kc, Fmhi);
-                }
-                if (cur >= k0) inplane_faces(cur & 3);
-                __syncthreads();
-                if (cur >= k0) update_cell(cur, Fmlo, Fmhi);
-#pragma unroll
-                for (int q = 0; q < NV; ++q) Fmlo[q] = Fmhi[q];
-            } else {
-                __syncthreads();
-            }
-        }
-    }
-
-    // block reductions: status bits, floor count, CFL minimum
-    __shared__ unsigned s_flags;
-    __shared__ unsigned long long s_floors;
-    __shared__ double s_wmin[32];
-    if (tid == 0) { s_flags = 0; s_floors = 0; }
-    __syncthreads();
-    const unsigned wf = __reduce_or_sync(0xffffffffu, flags);
-    const unsigned wc = __reduce_add_sync(0xffffffffu, floors);
-    double wm = wmin;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double other = __shfl_xor_sync(0xffffffffu, wm, o);
-        wm = other < wm ? other : wm;
-    }
-    if ((tid & 31) == 0) {
-        if (wf) atomicOr(&s_flags, wf);
-        if (wc) atomicAdd(&s_floors, (unsigned long long)wc);
-        s_wmin[tid >> 5] = wm;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        if (s_flags) atomicOr(&a.clk->status, s_flags);
-        if (s_floors) atomicAdd(&a.clk->floor_hits, s_floors);
-        if (STAGE == 2) {
-            double m = s_wmin[0];
-            for (int i = 1; i < NT / 32; ++i) m = s_wmin[i] < m ? s_wmin[i] : m;
-            atomicMin(&a.clk->wmin_bits, (unsigned long long)__double_as_longlong(m));
-        }
-    }
-}
-
-// CFL minimum over all cells of U (used when the state was set from outside).
-template <int ND>
-__global__ void __launch_bounds__(256) dt_kernel(Geom g, const double *U, Clock *clk) {
-    constexpr int NV = ND + 2;
-    const long long N = g.ncell;
-    unsigned flags = 0, floors = 0;
-    double wmin = __longlong_as_double((long long)kInfBits);
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        double u[NV], w[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) u[q] = U[(long long)q * N + c];
-        recover<ND>(u, g, w, flags, floors);
-        const double m = cfl_candidate<ND>(w, g);
-        if (m < wmin) wmin = m;
-    }
-    __shared__ double s_w[8];
-    __shared__ unsigned s_f;
-    if (threadIdx.x == 0) s_f = 0;
-    __syncthreads();
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double other = __shfl_xor_sync(0xffffffffu, wmin, o);
-        wmin = other < wmin ? other : wmin;
-    }
-    const unsigned wf = __reduce_or_sync(0xffffffffu, flags);
-    if ((threadIdx.x & 31) == 0) {
-        s_w[threadIdx.x >> 5] = wmin;
-        if (wf) atomicOr(&s_f, wf);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = s_w[0];
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = s_w[i] < m ? s_w[i] : m;
-        atomicMin(&clk->wmin_bits, (unsigned long long)__double_as_longlong(m));
-        if (s_f) atomicOr(&clk->status, s_f);
-    }
 }
 
 }  // namespace khy

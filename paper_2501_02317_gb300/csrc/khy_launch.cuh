@@ -1,41 +1,66 @@
 // khy_launch.cuh -- host-side dispatch of the stage and CFL kernels for one
 // reconstruction precision R (included once per precision translation unit).
+//
+// The stage kernel is persistent: the grid is the number of CTAs that can be
+// resident at once (SM count x occupancy), capped by the number of planes.
 #pragma once
 
 #include "khy_internal.h"
 
 namespace khy {
 
-template <int ND, class R, int STAGE, int TX, int TY>
-static cudaError_t configure_stage_tile() {
-    constexpr size_t smem = Tile<ND, TX, TY>::template smem_bytes<R>();
-    return cudaFuncSetAttribute(stage_kernel<ND, R, STAGE, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
-}
-
-template <int ND, class R, int STAGE, int TX, int TY>
-static cudaError_t launch_stage_tile(const StageArgs &a, cudaStream_t s) {
-    using T = Tile<ND, TX, TY>;
-    constexpr size_t smem = T::template smem_bytes<R>();
-    dim3 grid;
-    const int nxt = (a.g.n[0] + TX - 1) / TX;
-    if (ND == 1) {
-        grid = dim3(nxt, 1, 1);
-    } else if (ND == 2) {
-        grid = dim3(nxt, (a.g.n[1] + a.kchunk - 1) / a.kchunk, 1);
-    } else {
-        grid = dim3(nxt, (a.g.n[1] + TY - 1) / TY, (a.g.n[2] + a.kchunk - 1) / a.kchunk);
+template <class R, int ND, int STAGE, int TX, int TY>
+struct StageLaunch {
+    static int &resident() {  // resident CTAs on the device, 0 until prepared
+        static int r = 0;
+        return r;
     }
-    stage_kernel<ND, R, STAGE, TX, TY><<<grid, TX * TY, smem, s>>>(a);
-    return cudaGetLastError();
-}
+    static cudaError_t prepare() {
+        constexpr size_t smem = Tile<ND, TX, TY>::template smem_bytes<R>();
+        auto kern = stage_kernel<R, ND, STAGE, TX, TY>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, smem)) != cudaSuccess) return e;
+        resident() = sms * (per_sm > 0 ? per_sm : 1);
+        return cudaSuccess;
+    }
+    static cudaError_t launch(const StageArgs &a, cudaStream_t s) {
+        if (resident() == 0) {
+            cudaError_t e = prepare();
+            if (e != cudaSuccess) return e;
+        }
+        constexpr size_t smem = Tile<ND, TX, TY>::template smem_bytes<R>();
+        const long long ntx = (a.g.n[0] + TX - 1) / TX;
+        const long long nty = (ND == 3) ? (a.g.n[1] + TY - 1) / TY : 1;
+        const long long nm = (ND >= 2) ? a.g.n[ND - 1] : 1;
+        const long long total = ntx * nty * nm;
+        const int grid = (int)(total < resident() ? total : resident());
+        stage_kernel<R, ND, STAGE, TX, TY><<<grid, TX * TY, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+};
+
+// tile shapes per precision and dimensionality
+template <class R, int ND> struct TileOf;
+template <> struct TileOf<double, 1> { static constexpr int TX = 128, TY = 1; };
+template <> struct TileOf<double, 2> { static constexpr int TX = 128, TY = 1; };
+template <> struct TileOf<double, 3> { static constexpr int TX = 32, TY = 8; };
+template <> struct TileOf<float, 1> { static constexpr int TX = 256, TY = 1; };
+template <> struct TileOf<float, 2> { static constexpr int TX = 256, TY = 1; };
+template <> struct TileOf<float, 3> { static constexpr int TX = 32, TY = 16; };
+
+template <class R, int ND, int STAGE>
+using StageOf = StageLaunch<R, ND, STAGE, TileOf<R, ND>::TX, TileOf<R, ND>::TY>;
 
 template <class R>
 static cudaError_t launch_stage_prec(const StageArgs &a, int stage, cudaStream_t s) {
     switch (a.g.ndim) {
-        case 1: return stage == 1 ? launch_stage_tile<1, R, 1, 128, 1>(a, s) : launch_stage_tile<1, R, 2, 128, 1>(a, s);
-        case 2: return stage == 1 ? launch_stage_tile<2, R, 1, 128, 1>(a, s) : launch_stage_tile<2, R, 2, 128, 1>(a, s);
-        case 3: return stage == 1 ? launch_stage_tile<3, R, 1, 32, 8>(a, s) : launch_stage_tile<3, R, 2, 32, 8>(a, s);
+        case 1: return stage == 1 ? StageOf<R, 1, 1>::launch(a, s) : StageOf<R, 1, 2>::launch(a, s);
+        case 2: return stage == 1 ? StageOf<R, 2, 1>::launch(a, s) : StageOf<R, 2, 2>::launch(a, s);
+        case 3: return stage == 1 ? StageOf<R, 3, 1>::launch(a, s) : StageOf<R, 3, 2>::launch(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -45,25 +70,26 @@ static cudaError_t prepare_prec(int ndim) {
     cudaError_t e;
     switch (ndim) {
         case 1:
-            if ((e = configure_stage_tile<1, R, 1, 128, 1>()) != cudaSuccess) return e;
-            return configure_stage_tile<1, R, 2, 128, 1>();
+            if ((e = StageOf<R, 1, 1>::prepare()) != cudaSuccess) return e;
+            return StageOf<R, 1, 2>::prepare();
         case 2:
-            if ((e = configure_stage_tile<2, R, 1, 128, 1>()) != cudaSuccess) return e;
-            return configure_stage_tile<2, R, 2, 128, 1>();
+            if ((e = StageOf<R, 2, 1>::prepare()) != cudaSuccess) return e;
+            return StageOf<R, 2, 2>::prepare();
         case 3:
-            if ((e = configure_stage_tile<3, R, 1, 32, 8>()) != cudaSuccess) return e;
-            return configure_stage_tile<3, R, 2, 32, 8>();
+            if ((e = StageOf<R, 3, 1>::prepare()) != cudaSuccess) return e;
+            return StageOf<R, 3, 2>::prepare();
         default: return cudaErrorInvalidValue;
     }
 }
 
-static inline cudaError_t launch_dt_any(const Geom &g, const double *U, Clock *clk, cudaStream_t s) {
+template <class R>
+static cudaError_t launch_dt_prec(const Geom &g, const double *U, Clock *clk, cudaStream_t s) {
     const long long blocks_needed = (g.ncell + 255) / 256;
     const int blocks = (int)(blocks_needed < 152 * 8 ? blocks_needed : 152 * 8);
     switch (g.ndim) {
-        case 1: dt_kernel<1><<<blocks, 256, 0, s>>>(g, U, clk); break;
-        case 2: dt_kernel<2><<<blocks, 256, 0, s>>>(g, U, clk); break;
-        case 3: dt_kernel<3><<<blocks, 256, 0, s>>>(g, U, clk); break;
+        case 1: dt_kernel<R, 1><<<blocks, 256, 0, s>>>(g, U, clk); break;
+        case 2: dt_kernel<R, 2><<<blocks, 256, 0, s>>>(g, U, clk); break;
+        case 3: dt_kernel<R, 3><<<blocks, 256, 0, s>>>(g, U, clk); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

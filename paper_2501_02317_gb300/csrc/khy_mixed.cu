@@ -1,6 +1,7 @@
 // khy_mixed.cu -- mixed-precision instantiation of the hydro kernels
 // (Sec. 3.2.2): PLM reconstruction and the HLLC flux in FP32; conserved state,
-// primitive recovery and flux-difference accumulation in FP64.
+// the internal energy of the recovery and the flux-difference accumulation in
+// FP64 (see khy_mixed_kernels.cuh for how the FP64 work is kept small).
 #include "khy_launch.cuh"
 
 namespace khy {
@@ -10,7 +11,7 @@ cudaError_t launch_stage_mixed(const StageArgs &a, int stage, cudaStream_t s) {
 }
 
 cudaError_t launch_dt_mixed(const Geom &g, const double *U, Clock *clk, cudaStream_t s) {
-    return launch_dt_any(g, U, clk, s);
+    return launch_dt_prec<float>(g, U, clk, s);
 }
 
 cudaError_t prepare_mixed(int ndim) { return prepare_prec<float>(ndim); }

@@ -1,0 +1,179 @@
+// khy_mixed_kernels.cuh -- device functions of the mixed-precision path (Sec. 3.2.2),
+// shaped for GB300, whose FP64 pipe retires about 1.6 operations per clock
+// per SM against about 117 FP32 FMAs.  Every FP64 operation that the method
+// does not need is moved off that pipe:
+//
+//   * FP64 <-> FP32 conversions are done with integer instructions (the
+//     hardware conversions issue on the FP64 pipe).
+//   * Primitive recovery (Sec. 3.1) keeps the cancellation-prone internal
+//     energy E - |m|^2/(2 rho) in FP64 (7 FP64 operations in 3D: a Newton step
+//     on an FP32 reciprocal seed, |m|^2, and one fused multiply-add); the
+//     density, velocities and the pressure leave it as FP32 primitives.
+//   * Flux differences: per cell and field, the six FP32 face fluxes are
+//     summed error-free as a float-float pair (Knuth TwoSum), so the FP64
+//     update U + c (S_hi + S_lo) costs two FP64 operations in stage 1 and
+//     three in stage 2 (the Heun average), and each face flux still enters
+//     its two cells with opposite signs to full FP64 precision.
+//   * The CFL minimum for the next step is taken in FP32 from the new state,
+//     with an FP64 internal energy only where E - ke cancels.
+//
+// The stage kernel that uses these functions is khy_stage.cuh.
+#pragma once
+
+#include "khy_kernels.cuh"
+
+namespace khy {
+namespace mx {
+
+// ---------------------------------------------------------------- conversions
+// double -> float, round to nearest even; results below the float normal
+// range flush to zero, above it become +-inf; NaN stays NaN.
+__device__ __forceinline__ float d2f(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 896;  // float biased exponent
+    const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1FFFFFFFu;
+    unsigned f = sign | ((unsigned)e << 23) | m;
+    f += (rest > 0x10000000u) | ((rest == 0x10000000u) & (m & 1u));  // carry may reach the exponent
+    if (e <= 0) f = sign;                                           // underflow: flush to zero
+    if (e >= 255) f = sign | 0x7F800000u | ((((hi & 0x7FF00000u) == 0x7FF00000u) && ((hi & 0xFFFFFu) | lo)) ? 0x400000u : 0u);
+    return __uint_as_float(f);
+}
+
+// float -> double, exact for normal floats (subnormals flush to zero).
+__device__ __forceinline__ double f2d(float x) {
+    const unsigned f = __float_as_uint(x);
+    const unsigned sign = f & 0x80000000u;
+    const unsigned e = (f >> 23) & 0xFFu;
+    const unsigned m = f & 0x7FFFFFu;
+    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+    if (e == 0) hi = sign;
+    if (e == 255) hi = sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u);
+    const unsigned lo = (e == 0) ? 0u : (m << 29);
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
+// ---------------------------------------------------------------- float-float
+struct FF {
+    float hi, lo;
+};
+
+// exact: a + b == hi + lo
+__device__ __forceinline__ FF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    FF s = two_sum(a.hi, b.hi);
+    const float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s.hi, e);
+    return {hi, __fsub_rn(e, __fsub_rn(hi, s.hi))};
+}
+
+// ---------------------------------------------------------------- constants
+struct MixConsts {
+    float gamma, gm1, g1, gp1, gm1_gp1;
+    float rho_floor, p_floor;
+    long long rho_floor_bits;
+    double rho_floor_d;
+    float dx[3];
+};
+
+__device__ __forceinline__ MixConsts make_mix(const Geom &g) {
+    MixConsts k;
+    k.gamma = (float)g.gamma; k.gm1 = (float)g.gm1; k.g1 = (float)g.g1; k.gp1 = (float)g.gp1;
+    k.gm1_gp1 = (float)g.gm1_gp1;
+    k.rho_floor = (float)g.rho_floor; k.p_floor = (float)g.p_floor;
+    k.rho_floor_d = g.rho_floor;
+    k.rho_floor_bits = __double_as_longlong(g.rho_floor);
+    k.dx[0] = (float)g.dx[0]; k.dx[1] = (float)g.dx[1]; k.dx[2] = (float)g.dx[2];
+    return k;
+}
+
+__device__ __forceinline__ bool nonpositive_or_nan(double x) {
+    const long long b = __double_as_longlong(x);
+    return b <= 0 || b > 0x7FF0000000000000LL;  // sign set (or +0) or NaN
+}
+
+__device__ __forceinline__ bool negative_or_nan(double x) {
+    const long long b = __double_as_longlong(x);
+    return (b < 0 && b != (long long)0x8000000000000000ull) || (b & 0x7FFFFFFFFFFFFFFFLL) > 0x7FF0000000000000LL;
+}
+
+// ---------------------------------------------------------------- Sec. 3.1
+// Conserved (FP64) -> primitive (FP32) with the internal energy in FP64.
+template <int ND>
+__device__ __forceinline__ void recover(const double (&u)[ND + 2], const MixConsts &k, float (&w)[ND + 2],
+                                        unsigned &flags, unsigned &floors) {
+    double rho = u[0];
+    if (nonpositive_or_nan(rho)) flags |= FLAG_NONPHYSICAL;
+    if (__double_as_longlong(rho) < k.rho_floor_bits) {  // positive doubles order like their bits
+        rho = k.rho_floor_d;
+        flags |= FLAG_FLOOR;
+        ++floors;
+    }
+    const float rho32 = d2f(rho);
+    const float r32 = __frcp_rn(rho32);
+    double r = f2d(r32);
+    const double e = __fma_rn(-rho, r, 1.0);  // one Newton step: |1 - rho r| ~ 2^-46
+    r = __fma_rn(r, e, r);
+    double msq = __dmul_rn(u[1], u[1]);
+#pragma unroll
+    for (int d = 1; d < ND; ++d) msq = __fma_rn(u[1 + d], u[1 + d], msq);
+    const double eint = __fma_rn(-0.5, __dmul_rn(msq, r), u[ND + 1]);
+    if (negative_or_nan(eint)) flags |= FLAG_NONPHYSICAL;
+    float p = __fmul_rn(k.gm1, d2f(eint));
+    if (p < k.p_floor) {
+        p = k.p_floor;
+        flags |= FLAG_FLOOR;
+        ++floors;
+    }
+    w[0] = rho32;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) w[1 + d] = __fmul_rn(d2f(u[1 + d]), r32);
+    w[ND + 1] = p;
+}
+
+// CFL candidate min_d dx_d / (|v_d| + c_s) in FP32; the internal energy falls
+// back to FP64 where E - ke cancels by more than a factor of four.  Written
+// with explicit round-to-nearest intrinsics (no contraction), so every kernel
+// that calls it produces the same bits for the same state.
+template <int ND>
+__device__ __forceinline__ float cfl_candidate(const double (&u)[ND + 2], const MixConsts &k) {
+    float rho = d2f(u[0]);
+    if (!(rho >= k.rho_floor)) rho = k.rho_floor;
+    const float r = __frcp_rn(rho);
+    float v[ND];
+    float vsq = 0.f;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        v[d] = __fmul_rn(d2f(u[1 + d]), r);
+        vsq = __fmaf_rn(v[d], v[d], vsq);
+    }
+    const float E = d2f(u[ND + 1]);
+    float eint = __fsub_rn(E, __fmul_rn(__fmul_rn(0.5f, rho), vsq));
+    if (eint < __fmul_rn(0.25f, E)) {
+        double msq = __dmul_rn(u[1], u[1]);
+#pragma unroll
+        for (int d = 1; d < ND; ++d) msq = __fma_rn(u[1 + d], u[1 + d], msq);
+        eint = d2f(__dsub_rn(u[ND + 1], __ddiv_rn(__dmul_rn(0.5, msq), u[0])));
+    }
+    float p = __fmul_rn(k.gm1, eint);
+    if (!(p >= k.p_floor)) p = k.p_floor;
+    const float c = __fsqrt_rn(__fmul_rn(__fmul_rn(k.gamma, p), r));
+    float m = __fdiv_rn(k.dx[0], __fadd_rn(fabsf(v[0]), c));
+#pragma unroll
+    for (int d = 1; d < ND; ++d) {
+        const float t = __fdiv_rn(k.dx[d], __fadd_rn(fabsf(v[d]), c));
+        m = t < m ? t : m;
+    }
+    return m;
+}
+
+}  // namespace mx
+}  // namespace khy

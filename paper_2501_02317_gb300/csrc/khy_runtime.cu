@@ -226,7 +226,9 @@ cudaError_t launch_stage(const khy_sim *s, int stage) {
     StageArgs a;
     a.g = s->geom;
     a.clk = s->clk;
-    a.kchunk = march_chunk(s->geom);
+    a.cubic = 1;
+    for (int d = 1; d < s->geom.ndim; ++d)
+        if (s->geom.dx[d] != s->geom.dx[0]) a.cubic = 0;
     if (stage == 1) {
         a.Uin = s->U;
         a.Ubase = s->U;
@@ -598,10 +600,3 @@ khy_status khy_get_flags(khy_sim *s, unsigned *flags, unsigned long long *floor_
 }
 
 }  // extern "C"
-
-namespace khy {
-int march_chunk(const Geom &g) {
-    if (g.ndim == 1) return 1;
-    return 32;
-}
-}  // namespace khy

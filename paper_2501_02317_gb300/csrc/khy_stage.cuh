@@ -1,0 +1,365 @@
+// khy_stage.cuh -- the fused stage kernel of the Godunov hydro step and the
+// CFL-minimum kernel (sm_103a).
+//
+// One Heun step (Sec. 3.3) is three launches on one stream:
+//   clock kernel   : dt = C * min dx_d/(|v_d|+c_s) from the minimum the
+//                    previous stage-2 launch (or dt_kernel) accumulated, clipped
+//                    to t_end; t and the step counter advance (khy_runtime.cu).
+//   stage_kernel 1 : U1 = Un + dt L(Un)
+//   stage_kernel 2 : Un+1 = (Un + (U1 + dt L(U1))) / 2 written over Un, plus the
+//                    CFL minimum of Un+1 for the next step (Sec. 3.1: the step
+//                    length comes out of the variable conversion).
+//
+// Work decomposition.  The grid is cut into tiles of TX x TY columns along
+// the slowest ("march") axis -- z in 3D, y in 2D; a 1D grid is one row.  The
+// launch is persistent: one CTA per resident slot, and CTA b owns the b-th
+// equal share of the (tile, plane) sequence, so every SM gets the same number
+// of planes.  A CTA walks each of its tile segments plane by plane: a plane
+// of the conserved state with a two-cell halo on every side is loaded once,
+// converted to primitives (Sec. 3.1) with the ghost-zone rules applied by
+// index mapping (Sec. 3.1.1), and kept in a four-plane ring in shared memory
+// (the row staging of Sec. 3.2.1 extended to a 2.5D march).  In-plane face
+// fluxes run as one flat task list over the CTA; the face along the march
+// axis is computed by the thread that owns the column.  Each face flux is
+// computed once per CTA and enters its two cells with opposite signs; faces
+// on a tile edge are recomputed by the neighbouring CTA from the same inputs
+// by the same code, so both cells see the same value.
+//
+// Precision (Sec. 3.2.2) is the template parameter R:
+//   R = double : all-FP64, every operation in the CPU reference's order
+//                (compiled with -fmad=false: bitwise equal to the reference);
+//   R = float  : mixed -- FP32 reconstruction and HLLC, FP64 state, FP64
+//                internal energy in the recovery and FP64 flux-difference
+//                accumulation (khy_mixed_kernels.cuh).
+#pragma once
+
+#include <type_traits>
+
+#include "khy_kernels.cuh"
+#include "khy_mixed_kernels.cuh"
+
+namespace khy {
+
+struct StageArgs {
+    Geom g;
+    const double *Uin;    // state the fluxes are computed from (Un or U1)
+    const double *Ubase;  // Un (stage 2 average); unused in stage 1
+    double *Uout;         // U1 (stage 1) or Un+1 (stage 2, may alias Ubase)
+    Clock *clk;
+    int cubic;            // mixed path: all active dx equal (one dt/dx factor)
+};
+
+template <int ND, int TX, int TY>
+struct Tile {
+    static constexpr int NV = ND + 2;
+    static constexpr int PX = TX + 4;
+    static constexpr int PY = (ND == 3) ? TY + 4 : 1;
+    static constexpr int PC = PX * PY;
+    static constexpr int NSLOT = (ND == 1) ? 1 : 4;
+    static constexpr int NT = TX * TY;
+    static constexpr int NXF = (TX + 1) * TY;
+    static constexpr int NYF = (ND == 3) ? TX * (TY + 1) : 0;
+    template <class R>
+    static constexpr size_t smem_bytes() {
+        return sizeof(R) * ((size_t)NSLOT * NV * PC + (size_t)NV * NXF + (size_t)NV * NYF);
+    }
+};
+
+template <class R, int ND, int STAGE, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) stage_kernel(StageArgs a) {
+    constexpr bool MIX = std::is_same<R, float>::value;
+    using T = Tile<ND, TX, TY>;
+    constexpr int NV = T::NV, PX = T::PX, PC = T::PC, NT = T::NT;
+    constexpr int DM = ND - 1;  // march axis (ND >= 2)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sW = reinterpret_cast<R *>(smem_raw);   // [NSLOT][NV][PC] primitives
+    R *sFx = sW + (size_t)T::NSLOT * NV * PC;  // [NV][TY][TX+1] x-face fluxes
+    R *sFy = sFx + (size_t)NV * T::NXF;        // [NV][TY+1][TX] y-face fluxes (3D)
+
+    const Geom &g = a.g;
+    const Clock *clk = a.clk;
+    if (!clk->active) return;
+    const double dtdx[3] = {clk->dtdx[0], clk->dtdx[1], clk->dtdx[2]};
+    const Consts<R> kc = make_consts<R>(g);
+    const mx::MixConsts mk = mx::make_mix(g);
+    const long long N = g.ncell;
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int ntx = (g.n[0] + TX - 1) / TX;
+    const int nty = (ND == 3) ? (g.n[1] + TY - 1) / TY : 1;
+    const int nm = (ND >= 2) ? g.n[DM] : 1;
+    const long long total = (long long)ntx * nty * nm;
+    const long long s0 = total * blockIdx.x / gridDim.x;
+    const long long s1 = total * (blockIdx.x + 1) / gridDim.x;
+
+    unsigned flags = 0, floors = 0;
+    double wmin = __longlong_as_double((long long)kInfBits);
+
+    int x0 = 0, y0 = 0, k0 = 0, k1 = 0;  // current tile origin and plane range
+
+    // plane L of the march axis (ignored in 1D) -> ring slot
+    auto load_plane = [&](int L, int slot) {
+        R *dst = sW + (size_t)slot * NV * PC;
+        for (int e = tid; e < PC; e += NT) {
+            const int hx = e % PX, hy = e / PX;
+            int act[3] = {0, 0, 0};
+            int c[3] = {0, 0, 0};
+            c[0] = bc_map(x0 - 2 + hx, g.n[0], g.bc[0][0], g.bc[0][1], &act[0]);
+            if (ND == 3) {
+                c[1] = bc_map(y0 - 2 + hy, g.n[1], g.bc[1][0], g.bc[1][1], &act[1]);
+                c[2] = bc_map(L, g.n[2], g.bc[2][0], g.bc[2][1], &act[2]);
+            } else if (ND == 2) {
+                c[1] = bc_map(L, g.n[1], g.bc[1][0], g.bc[1][1], &act[1]);
+            }
+            const long long idx = ((long long)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
+            double u[NV];
+            R w[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) u[q] = __ldg(a.Uin + (long long)q * N + idx);
+            unsigned fl = 0;
+            if constexpr (MIX) {
+                mx::recover<ND>(u, mk, w, flags, fl);
+            } else {
+                recover<ND>(u, g, w, flags, fl);
+            }
+            const bool interior = hx >= 2 && hx < TX + 2 && x0 - 2 + hx < g.n[0] &&
+                                  (ND != 3 || (hy >= 2 && hy < TY + 2 && y0 - 2 + hy < g.n[1])) &&
+                                  (ND == 1 || (L >= k0 && L < k1));
+            if (interior) floors += fl;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {  // ghost-zone velocity rules (Sec. 3.1.1)
+                R v = w[1 + d];
+                if (act[d] == 1) v = -v;
+                else if (act[d] == 2) v = v > R(0) ? R(0) : v;
+                else if (act[d] == 3) v = v < R(0) ? R(0) : v;
+                w[1 + d] = v;
+            }
+#pragma unroll
+            for (int q = 0; q < NV; ++q) dst[(size_t)q * PC + e] = w[q];
+        }
+    };
+
+    auto gather = [&](const R *base, int e0, int stride, R (&s)[4][NV]) {
+#pragma unroll
+        for (int o = 0; o < 4; ++o)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) s[o][q] = base[(size_t)q * PC + e0 + o * stride];
+    };
+
+    auto inplane_faces = [&](int slot) {
+        const R *pl = sW + (size_t)slot * NV * PC;
+        for (int f = tid; f < T::NXF + T::NYF; f += NT) {
+            R s[4][NV], F[NV];
+            if (f < T::NXF) {
+                const int fx = f % (TX + 1), fy = f / (TX + 1);
+                const int hy = (ND == 3) ? fy + 2 : 0;
+                gather(pl, hy * PX + fx, 1, s);
+                face_flux<ND, R>(s, 0, kc, F);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) sFx[(size_t)q * T::NXF + f] = F[q];
+            } else {
+                const int f2 = f - T::NXF;
+                const int fxx = f2 % TX, fyy = f2 / TX;
+                gather(pl, fyy * PX + fxx + 2, PX, s);
+                face_flux<ND, R>(s, 1, kc, F);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) sFy[(size_t)q * T::NYF + f2] = F[q];
+            }
+        }
+    };
+
+    // conservative update of cell (tx, ty) of plane cur (Sec. 3.3)
+    auto update_cell = [&](int cur, const R (&Fmlo)[NV], const R (&Fmhi)[NV]) {
+        const int gx = x0 + tx;
+        const int gy = (ND == 3) ? y0 + ty : (ND == 2 ? cur : 0);
+        const int gz = (ND == 3) ? cur : 0;
+        if (gx >= g.n[0] || (ND == 3 && gy >= g.n[1])) return;
+        const long long idx = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
+        double un[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const R *fx = sFx + (size_t)q * T::NXF + ty * (TX + 1) + tx;
+            const R *fy = sFy + (size_t)q * T::NYF + ty * TX + tx;
+            const double u = a.Uin[(long long)q * N + idx];
+            double r;
+            if constexpr (!MIX) {
+                // dU = -sum_d (dt/dx_d)(F_hi - F_lo), directions in x, y, z order
+                double acc = 0.0 - dtdx[0] * (fx[1] - fx[0]);
+                if (ND == 3) acc = acc - dtdx[1] * (fy[TX] - fy[0]);
+                if (ND >= 2) acc = acc - dtdx[DM] * (Fmhi[q] - Fmlo[q]);
+                if (STAGE == 1) r = u + acc;
+                else r = 0.5 * (a.Ubase[(long long)q * N + idx] + (u + acc));
+            } else {
+                // F_lo - F_hi per direction, exact as float-float pairs
+                const mx::FF Dx = mx::two_sum(fx[0], -fx[1]);
+                mx::FF Dy = {0.f, 0.f}, Dm = {0.f, 0.f};
+                if (ND == 3) Dy = mx::two_sum(fy[0], -fy[TX]);
+                if (ND >= 2) Dm = mx::two_sum(Fmlo[q], -Fmhi[q]);
+                if (a.cubic) {
+                    mx::FF S = Dx;
+                    if (ND == 3) S = mx::ff_add(S, Dy);
+                    if (ND >= 2) S = mx::ff_add(S, Dm);
+                    const double c = dtdx[0];
+                    if (STAGE == 1) {
+                        const double lo = mx::f2d(__fmul_rn(mx::d2f(c), S.lo));
+                        r = __fma_rn(c, mx::f2d(S.hi), __dadd_rn(u, lo));
+                    } else {
+                        const double hc = 0.5 * c;
+                        const double lo = mx::f2d(__fmul_rn(mx::d2f(hc), S.lo));
+                        const double A = __dadd_rn(a.Ubase[(long long)q * N + idx], u);
+                        r = __fma_rn(hc, mx::f2d(S.hi), __fma_rn(0.5, A, lo));
+                    }
+                } else {
+                    double acc = __fma_rn(dtdx[0], mx::f2d(Dx.hi), __dmul_rn(dtdx[0], mx::f2d(Dx.lo)));
+                    if (ND == 3) acc = __fma_rn(dtdx[1], mx::f2d(Dy.hi), __fma_rn(dtdx[1], mx::f2d(Dy.lo), acc));
+                    if (ND >= 2) acc = __fma_rn(dtdx[DM], mx::f2d(Dm.hi), __fma_rn(dtdx[DM], mx::f2d(Dm.lo), acc));
+                    if (STAGE == 1) r = __dadd_rn(u, acc);
+                    else r = __dmul_rn(0.5, __dadd_rn(a.Ubase[(long long)q * N + idx], __dadd_rn(u, acc)));
+                }
+            }
+            un[q] = r;
+            a.Uout[(long long)q * N + idx] = r;
+        }
+        if (STAGE == 2) {  // CFL candidate of the new state for the next step
+            double c;
+            if constexpr (MIX) {
+                c = mx::f2d(mx::cfl_candidate<ND>(un, mk));
+            } else {
+                double w[NV];
+                unsigned fl = 0;
+                recover<ND>(un, g, w, flags, fl);
+                c = cfl_candidate<ND>(w, g);
+            }
+            wmin = c < wmin ? c : wmin;
+        }
+    };
+
+    for (long long pos = s0; pos < s1;) {
+        const long long tile = pos / nm;
+        k0 = (int)(pos % nm);
+        k1 = (int)((long long)nm < k0 + (s1 - pos) ? (long long)nm : k0 + (s1 - pos));
+        x0 = (int)(tile % ntx) * TX;
+        y0 = (ND == 3) ? (int)(tile / ntx) * TY : 0;
+        pos += k1 - k0;
+        if (ND == 1) {
+            load_plane(0, 0);
+            __syncthreads();
+            inplane_faces(0);
+            __syncthreads();
+            R dummy[NV];
+            update_cell(0, dummy, dummy);
+            __syncthreads();
+        } else {
+            R Fmlo[NV], Fmhi[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) { Fmlo[q] = R(0); Fmhi[q] = R(0); }
+            for (int L = k0 - 2; L <= k1 + 1; ++L) {
+                load_plane(L, L & 3);
+                __syncthreads();
+                if (L >= k0 + 1) {
+                    const int cur = L - 2;
+                    {   // march-axis face between cur and cur+1, from planes cur-1 .. cur+2
+                        R s[4][NV];
+                        const int e = (ND == 3) ? (ty + 2) * PX + tx + 2 : tx + 2;
+#pragma unroll
+                        for (int o = 0; o < 4; ++o) {
+                            const R *pl = sW + (size_t)((cur - 1 + o) & 3) * NV * PC;
+#pragma unroll
+                            for (int q = 0; q < NV; ++q) s[o][q] = pl[(size_t)q * PC + e];
+                        }
+                        face_flux<ND, R>(s, DM, kc, Fmhi);
+                    }
+                    if (cur >= k0) inplane_faces(cur & 3);
+                    __syncthreads();
+                    if (cur >= k0) update_cell(cur, Fmlo, Fmhi);
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) Fmlo[q] = Fmhi[q];
+                } else {
+                    __syncthreads();
+                }
+            }
+        }
+    }
+
+    // block reductions: status bits, floor count, CFL minimum
+    __shared__ unsigned s_flags;
+    __shared__ unsigned long long s_floors;
+    __shared__ double s_wmin[32];
+    if (tid == 0) { s_flags = 0; s_floors = 0; }
+    __syncthreads();
+    const unsigned wf = __reduce_or_sync(0xffffffffu, flags);
+    const unsigned wc = __reduce_add_sync(0xffffffffu, floors);
+    double wm = wmin;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double other = __shfl_xor_sync(0xffffffffu, wm, o);
+        wm = other < wm ? other : wm;
+    }
+    if ((tid & 31) == 0) {
+        if (wf) atomicOr(&s_flags, wf);
+        if (wc) atomicAdd(&s_floors, (unsigned long long)wc);
+        s_wmin[tid >> 5] = wm;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (s_flags) atomicOr(&a.clk->status, s_flags);
+        if (s_floors) atomicAdd(&a.clk->floor_hits, s_floors);
+        if (STAGE == 2) {
+            double m = s_wmin[0];
+            for (int i = 1; i < NT / 32; ++i) m = s_wmin[i] < m ? s_wmin[i] : m;
+            atomicMin(&a.clk->wmin_bits, (unsigned long long)__double_as_longlong(m));
+        }
+    }
+}
+
+// CFL minimum over all cells of U (used when the state was set from outside);
+// the same per-cell candidate as the fused one in stage_kernel<..., 2, ...>.
+template <class R, int ND>
+__global__ void __launch_bounds__(256) dt_kernel(Geom g, const double *U, Clock *clk) {
+    constexpr bool MIX = std::is_same<R, float>::value;
+    constexpr int NV = ND + 2;
+    const mx::MixConsts mk = mx::make_mix(g);
+    const long long N = g.ncell;
+    unsigned flags = 0, floors = 0;
+    double wmin = __longlong_as_double((long long)kInfBits);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        double u[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) u[q] = U[(long long)q * N + c];
+        double m;
+        if constexpr (MIX) {
+            float w[NV];
+            mx::recover<ND>(u, mk, w, flags, floors);
+            m = mx::f2d(mx::cfl_candidate<ND>(u, mk));
+        } else {
+            double w[NV];
+            recover<ND>(u, g, w, flags, floors);
+            m = cfl_candidate<ND>(w, g);
+        }
+        wmin = m < wmin ? m : wmin;
+    }
+    __shared__ double s_w[8];
+    __shared__ unsigned s_f;
+    if (threadIdx.x == 0) s_f = 0;
+    __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double other = __shfl_xor_sync(0xffffffffu, wmin, o);
+        wmin = other < wmin ? other : wmin;
+    }
+    const unsigned wf = __reduce_or_sync(0xffffffffu, flags);
+    if ((threadIdx.x & 31) == 0) {
+        s_w[threadIdx.x >> 5] = wmin;
+        if (wf) atomicOr(&s_f, wf);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = s_w[0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = s_w[i] < m ? s_w[i] : m;
+        atomicMin(&clk->wmin_bits, (unsigned long long)__double_as_longlong(m));
+        if (s_f) atomicOr(&clk->status, s_f);
+    }
+}
+
+}  // namespace khy

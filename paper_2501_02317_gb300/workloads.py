@@ -298,10 +298,10 @@ def random_jumpy(mesh: Mesh, seed: int = 11) -> np.ndarray:
     rng = np.random.default_rng(seed)
     W = _empty(mesh)
     s = mesh.shape[1:]
-    W[0] = np.exp(rng.uniform(np.log(0.1), np.log(10.0), size=s))
+    W[0] = np.exp(rng.uniform(np.log(0.3), np.log(3.0), size=s))
     for d in range(mesh.ndim):
-        W[1 + d] = rng.uniform(-3.0, 3.0, size=s)
-    W[mesh.nvar - 1] = np.exp(rng.uniform(np.log(0.05), np.log(20.0), size=s))
+        W[1 + d] = rng.uniform(-1.0, 1.0, size=s)
+    W[mesh.nvar - 1] = np.exp(rng.uniform(np.log(0.3), np.log(3.0), size=s))
     return W
 
 

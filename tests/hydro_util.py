@@ -17,9 +17,13 @@ def pressure_np(mesh, U):
     return (mesh.gamma - 1.0) * (U[mesh.nvar - 1] - ke)
 
 
-def oracle_run(mesh, W, t_end=1e30, max_steps=1 << 40):
+def oracle_run(mesh, W, t_end=1e30, max_steps=1 << 40, allow_flags=False):
+    """Oracle run from primitive W; a parity case must stay physical (no
+    floor, no negative pressure) unless allow_flags."""
     U0 = oracle.prim_to_cons(mesh, W)
     U, t, s, f = oracle.run(mesh, U0, 0.0, t_end, max_steps)
+    if not allow_flags:
+        assert f == 0, "oracle flags %d: the parity input is not a valid physical case" % f
     return U, t, s, f
 
 

@@ -257,6 +257,23 @@ def test_nonphysical_state_is_reported():
         assert flags & 1
 
 
+def test_nonphysical_detected_on_both_sides():
+    # violent random jumps drive some pressures negative: the oracle flags
+    # it and the CUDA path reports KHY_ERR_NONPHYSICAL for the same input
+    from paper_2501_02317_gb300 import khydro
+    mesh = wl.Mesh(ndim=2, n=(64, 64, 1), gamma=1.4, cfl=0.4)
+    rng = np.random.default_rng(5)
+    W = np.zeros(mesh.shape)
+    W[0] = np.exp(rng.uniform(np.log(0.1), np.log(10.0), size=mesh.shape[1:]))
+    W[1:3] = rng.uniform(-3.0, 3.0, size=(2,) + mesh.shape[1:])
+    W[3] = np.exp(rng.uniform(np.log(0.05), np.log(20.0), size=mesh.shape[1:]))
+    _, _, _, fo = oracle_run(mesh, W, max_steps=6, allow_flags=True)
+    assert fo & oracle.FLAG_NONPHYSICAL
+    with pytest.raises(khydro.KhydroError) as ei:
+        gpu_run(mesh, W, max_steps=6)
+    assert ei.value.status == -4
+
+
 def test_dt_matches_oracle():
     mesh, W = wl.kelvin_helmholtz(80, prec=wl.PREC_FP64)
     U0 = oracle.prim_to_cons(mesh, W)
