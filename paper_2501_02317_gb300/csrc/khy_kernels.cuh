@@ -140,6 +140,23 @@ __device__ __forceinline__ Consts<R> make_consts(const Geom &g) {
     return c;
 }
 
+// ------------------------------------------------------------ pinned arithmetic
+// Every floating-point operation of the face flux goes through these
+// round-to-nearest intrinsics, so the compiler cannot fuse or reorder them:
+// a face flux computed by two different CTAs (or two unrolled copies of a
+// loop) from the same inputs has the same bits, which is what makes the
+// flux-difference update conservative to round-off.
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double rsqrt_(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float rsqrt_(float a) { return __fsqrt_rn(a); }
+
 // ------------------------------------------------------------ Sec. 3.2.2
 // HLLC flux for rotated primitive states w = (rho, u, t_1..t_NT, p), NT
 // transverse velocity components.  Output F = (mass, normal momentum,
@@ -150,26 +167,31 @@ __device__ __forceinline__ void hllc(const Consts<R> &k, const R (&wl)[NT + 3], 
     constexpr int P = NT + 2;  // pressure slot
     const R rl = wl[0], ul = wl[1], pl = wl[P];
     const R rr = wr[0], ur = wr[1], pr = wr[P];
-    const R cl = sqrt(k.gamma * pl / rl);
-    const R cr = sqrt(k.gamma * pr / rr);
-    R ppv = R(0.5) * (pl + pr) - R(0.125) * (ur - ul) * (rl + rr) * (cl + cr);
+    const R cl = rsqrt_(rdiv(rmul(k.gamma, pl), rl));
+    const R cr = rsqrt_(rdiv(rmul(k.gamma, pr), rr));
+    // p* estimate: PVRS clamped at 0; the two-shock estimate when both waves are shocks
+    const R ppv = rsub(rmul(R(0.5), radd(pl, pr)),
+                       rmul(rmul(rmul(R(0.125), rsub(ur, ul)), radd(rl, rr)), radd(cl, cr)));
     R pstar = ppv > R(0) ? ppv : R(0);
-    R pmax = pl > pr ? pl : pr;
-    if (pstar > pmax) {  // both waves are shocks: two-shock estimate
-        R gl = sqrt((R(2) / (k.gp1 * rl)) / (pstar + k.gm1_gp1 * pl));
-        R gr = sqrt((R(2) / (k.gp1 * rr)) / (pstar + k.gm1_gp1 * pr));
-        pstar = (gl * pl + gr * pr - (ur - ul)) / (gl + gr);
+    const R pmax = pl > pr ? pl : pr;
+    if (pstar > pmax) {
+        const R gl = rsqrt_(rdiv(rdiv(R(2), rmul(k.gp1, rl)), radd(pstar, rmul(k.gm1_gp1, pl))));
+        const R gr = rsqrt_(rdiv(rdiv(R(2), rmul(k.gp1, rr)), radd(pstar, rmul(k.gm1_gp1, pr))));
+        pstar = rdiv(rsub(radd(rmul(gl, pl), rmul(gr, pr)), rsub(ur, ul)), radd(gl, gr));
     }
-    R ratl = pstar / pl, ratr = pstar / pr;
+    R ratl = rdiv(pstar, pl), ratr = rdiv(pstar, pr);
     if (ratl < R(1)) ratl = R(1);
     if (ratr < R(1)) ratr = R(1);
-    const R ql = sqrt(R(1) + k.g1 * (ratl - R(1)));
-    const R qr = sqrt(R(1) + k.g1 * (ratr - R(1)));
-    const R dsl = -cl * ql;
-    const R dsr = cr * qr;
-    const R sl = ul + dsl;
-    const R sr = ur + dsr;
-    const R sstar = ((pr - rr * ur * dsr) - (pl - rl * ul * dsl)) / (rl * dsl - rr * dsr);
+    // Eq. 5: q_K and the subtraction-safe offsets ds_K = s_K - u_K
+    const R ql = rsqrt_(radd(R(1), rmul(k.g1, rsub(ratl, R(1)))));
+    const R qr = rsqrt_(radd(R(1), rmul(k.g1, rsub(ratr, R(1)))));
+    const R dsl = rmul(-cl, ql);
+    const R dsr = rmul(cr, qr);
+    const R sl = radd(ul, dsl);
+    const R sr = radd(ur, dsr);
+    // Eq. 4 with s_K - u_K replaced by ds_K
+    const R sstar = rdiv(rsub(rsub(pr, rmul(rmul(rr, ur), dsr)), rsub(pl, rmul(rmul(rl, ul), dsl))),
+                         rsub(rmul(rl, dsl), rmul(rr, dsr)));
 
     // Branches in the reference order: 0 <= s_L -> F_L; 0 <= s* -> F*_L;
     // 0 < s_R -> F*_R; else F_R.  Only the selected side's states are built.
@@ -181,32 +203,37 @@ __device__ __forceinline__ void hllc(const Consts<R> &k, const R (&wl)[NT + 3], 
     const R rk = w[0], uk = w[1], pk = w[P];
     const R sk = left ? sl : sr;
     const R dsk = left ? dsl : dsr;
-    R vsq = uk * uk;
+    R vsq = rmul(uk, uk);
 #pragma unroll
-    for (int j = 0; j < NT; ++j) vsq = vsq + w[2 + j] * w[2 + j];
-    const R E = pk / k.gm1 + R(0.5) * rk * vsq;
-    const R mf = rk * uk;
+    for (int j = 0; j < NT; ++j) vsq = radd(vsq, rmul(w[2 + j], w[2 + j]));
+    const R E = radd(rdiv(pk, k.gm1), rmul(rmul(R(0.5), rk), vsq));
+    const R mf = rmul(rk, uk);
     R Uk[NT + 3], Fk[NT + 3];
-    Uk[0] = rk; Uk[1] = rk * uk;
-    Fk[0] = mf; Fk[1] = mf * uk + pk;
+    Uk[0] = rk;
+    Uk[1] = rmul(rk, uk);
+    Fk[0] = mf;
+    Fk[1] = radd(rmul(mf, uk), pk);
 #pragma unroll
-    for (int j = 0; j < NT; ++j) { Uk[2 + j] = rk * w[2 + j]; Fk[2 + j] = mf * w[2 + j]; }
+    for (int j = 0; j < NT; ++j) {
+        Uk[2 + j] = rmul(rk, w[2 + j]);
+        Fk[2 + j] = rmul(mf, w[2 + j]);
+    }
     Uk[P] = E;
-    Fk[P] = (E + pk) * uk;
+    Fk[P] = rmul(radd(E, pk), uk);
     if (outside) {
 #pragma unroll
         for (int q = 0; q < NT + 3; ++q) F[q] = Fk[q];
         return;
     }
-    const R fac = rk * dsk / (sk - sstar);
+    const R fac = rdiv(rmul(rk, dsk), rsub(sk, sstar));
     R Us[NT + 3];
     Us[0] = fac;
-    Us[1] = fac * sstar;
+    Us[1] = rmul(fac, sstar);
 #pragma unroll
-    for (int j = 0; j < NT; ++j) Us[2 + j] = fac * w[2 + j];
-    Us[P] = fac * (Uk[P] / rk + (sstar - uk) * (sstar + pk / (rk * dsk)));
+    for (int j = 0; j < NT; ++j) Us[2 + j] = rmul(fac, w[2 + j]);
+    Us[P] = rmul(fac, radd(rdiv(Uk[P], rk), rmul(rsub(sstar, uk), radd(sstar, rdiv(pk, rmul(rk, dsk))))));
 #pragma unroll
-    for (int q = 0; q < NT + 3; ++q) F[q] = Fk[q] + sk * (Us[q] - Uk[q]);
+    for (int q = 0; q < NT + 3; ++q) F[q] = radd(Fk[q], rmul(sk, rsub(Us[q], Uk[q])));
 }
 
 // Face flux from the four primitive cells around a face along direction dir
@@ -229,10 +256,10 @@ __device__ __forceinline__ void face_flux(const R (&s)[4][ND + 2], int dir, cons
     for (int j = 0; j < ND + 2; ++j) {
         const int q = slot[j];
         const R s0 = s[0][q], s1 = s[1][q], s2 = s[2][q], s3 = s[3][q];
-        R a = minmod<R>(s1 - s0, s2 - s1);
-        wl[j] = s1 + R(0.5) * a;
-        R b = minmod<R>(s2 - s1, s3 - s2);
-        wr[j] = s2 - R(0.5) * b;
+        const R a = minmod<R>(rsub(s1, s0), rsub(s2, s1));
+        wl[j] = radd(s1, rmul(R(0.5), a));
+        const R b = minmod<R>(rsub(s2, s1), rsub(s3, s2));
+        wr[j] = rsub(s2, rmul(R(0.5), b));
     }
     R Fr[NT + 3];
     hllc<R, NT>(k, wl, wr, Fr);

@@ -212,21 +212,25 @@ def test_set_primitive_matches_oracle_conversion():
 
 
 def test_split_run_equals_straight_run():
-    # checkpoint/resume: U and t are the whole state of the method
+    # checkpoint/resume: U and t are the whole state of the method, so a run
+    # stopped after some steps, saved, and resumed in a fresh simulation is
+    # bitwise equal to the straight run (both precisions)
     from paper_2501_02317_gb300 import khydro
-    mesh, W = wl.kelvin_helmholtz(96, prec=wl.PREC_MIXED)
-    Ua, ta, sa, _ = gpu_run(mesh, W, 0.1)
-    with khydro.Sim(mesh) as sim:
-        sim.set_primitive(W)
-        sim.step_to(0.04)
-        Umid = sim.conserved()
-        tmid, _, _ = sim.time()
-    with khydro.Sim(mesh) as sim2:
-        sim2.set_conserved(Umid)
-        sim2.set_time(tmid)
-        sim2.step_to(0.1)
-        Ub = sim2.conserved()
-    np.testing.assert_array_equal(Ua, Ub)
+    for prec in (wl.PREC_MIXED, wl.PREC_FP64):
+        mesh, W = wl.kelvin_helmholtz(96, prec=prec)
+        Ua, ta, sa, _ = gpu_run(mesh, W, max_steps=20)
+        with khydro.Sim(mesh) as sim:
+            sim.set_primitive(W)
+            sim.step_to(1e30, 8)
+            Umid = sim.conserved()
+            tmid, _, _ = sim.time()
+        with khydro.Sim(mesh) as sim2:
+            sim2.set_conserved(Umid)
+            sim2.set_time(tmid)
+            s2, t2 = sim2.step_to(1e30, 12)
+            Ub = sim2.conserved()
+        assert s2 == 12 and t2 == ta
+        np.testing.assert_array_equal(Ua, Ub)
 
 
 def test_step_to_lands_on_t_end_and_respects_max_steps():
