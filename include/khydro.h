@@ -148,6 +148,41 @@ khy_status khy_totals(khy_sim *sim, double out[5]);
  * applied) and the number of floor applications; clears them when clear != 0. */
 khy_status khy_get_flags(khy_sim *sim, unsigned *flags, unsigned long long *floor_hits, int clear);
 
+/* ------------------------------------------------------------ no allocation */
+
+/* Capacity, in bytes, of the stage-1 scratch state that khy_step_noalloc
+ * keeps in a file-scope device array: it steps meshes with
+ * nvar * ncell * 8 <= KHY_NOALLOC_SCRATCH_BYTES (e.g. 1024^2 in 2D, 96^3 in 3D). */
+#define KHY_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* One Heun step that allocates nothing (the paper has no counterpart: this
+ * is an interface for callers that cannot call cudaMalloc when they step --
+ * a host program that reserves all device memory for its own pool, a
+ * real-time loop that cannot take the device synchronisation cudaMalloc and
+ * cudaFree may cause, or a plug-in whose host application owns every
+ * allocation).
+ *
+ * Advances the conserved state U_dev (device memory, nvar*ncell doubles,
+ * field-major, in and out) by one Heun step from time t toward t_end, exactly
+ * as one step of khy_step_to: dt from the CFL condition on U_dev, clipped so
+ * the step lands on t_end; no step when t >= t_end.  Writes three doubles to
+ * the device buffer out_dev: the new time, the dt taken (0 if none) and the
+ * status bits (1 = non-physical state seen, 2 = a floor was applied).
+ * Stream-ordered on cuda_stream (may be NULL), no host synchronisation.
+ *
+ * Scratch: U^1 and the step clock live in one file-scope __device__ array of
+ * KHY_NOALLOC_SCRATCH_BYTES + 256 bytes that every GPU which loads the library
+ * holds until the process exits; no cudaMalloc, cudaFree or allocating
+ * library routine is called.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call shares the
+ * array: calls whose work overlaps on the GPU (other streams or threads)
+ * race.  Errors: KHY_ERR_ARG for an invalid descriptor, NULL pointers, NaN
+ * times, or a state larger than the scratch (the message gives both sizes);
+ * KHY_ERR_CUDA if a launch fails. */
+khy_status khy_step_noalloc(const khy_mesh_desc *desc, double *U_dev, double t, double t_end, double *out_dev,
+                            void *cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *khy_last_error(void);
 

@@ -1,10 +1,11 @@
 """Builds libkhydro.so in-tree with nvcc for sm_103a (GB300).
 
-Three translation units are compiled in parallel and linked into one shared
+The translation units are compiled in parallel and linked into one shared
 library:
   * khy_fp64.cu    -- all-FP64 kernels, -fmad=false (bitwise-reproducible)
   * khy_mixed.cu   -- mixed-precision kernels (FP32 flux, FP64 state)
   * khy_runtime.cu -- C ABI, simulation objects, graphs, -fmad=false
+  * khy_noalloc.cu -- the allocation-free one-step entry point
 
 ``python -m paper_2501_02317_gb300.build`` builds; ``build()`` is what
 ``__graft_entry__.build()`` calls.
@@ -31,6 +32,7 @@ UNITS = {
     "khy_fp64": ["-fmad=false"],
     "khy_mixed": [],
     "khy_runtime": ["-fmad=false"],
+    "khy_noalloc": ["-fmad=false"],
 }
 
 

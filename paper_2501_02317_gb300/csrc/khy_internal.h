@@ -23,3 +23,14 @@ cudaError_t prepare_fp64(int ndim);
 cudaError_t prepare_mixed(int ndim);
 
 }  // namespace khy
+
+// Runtime helpers shared with khy_noalloc.cu (implemented in khy_runtime.cu).
+
+struct khy_mesh_desc;
+
+namespace khy {
+int validate_desc(const khy_mesh_desc *d);             // khy_status of the descriptor check
+Geom geom_of_desc(const khy_mesh_desc &d);
+int record_error(int status, const char *msg);         // sets khy_last_error(), returns status
+cudaError_t launch_clock_step(Clock *c, const Geom &g, cudaStream_t s);
+}  // namespace khy

@@ -600,3 +600,19 @@ khy_status khy_get_flags(khy_sim *s, unsigned *flags, unsigned long long *floor_
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ helpers for khy_noalloc.cu
+
+namespace khy {
+int validate_desc(const khy_mesh_desc *d) {
+    khy_status st = validate(d);
+    if (st != KHY_OK) return st;
+    return check_periodic_pairs(*d);
+}
+Geom geom_of_desc(const khy_mesh_desc &d) { return make_geom(d); }
+int record_error(int status, const char *msg) { return fail((khy_status)status, "%s", msg); }
+cudaError_t launch_clock_step(Clock *c, const Geom &g, cudaStream_t s) {
+    clock_step_kernel<<<1, 1, 0, s>>>(c, g);
+    return cudaGetLastError();
+}
+}  // namespace khy

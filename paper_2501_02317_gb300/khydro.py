@@ -32,7 +32,7 @@ EXPORTS = [
     "khy_create", "khy_destroy", "khy_set_boundary", "khy_set_conserved", "khy_set_primitive",
     "khy_set_conserved_dev", "khy_set_primitive_dev", "khy_set_time", "khy_step_to",
     "khy_enqueue_steps", "khy_get_conserved", "khy_get_conserved_dev", "khy_get_time", "khy_totals",
-    "khy_get_flags", "khy_last_error", "khy_version", "khy_profile_steps",
+    "khy_get_flags", "khy_last_error", "khy_version", "khy_profile_steps", "khy_step_noalloc",
 ]
 
 
@@ -104,6 +104,7 @@ def lib() -> ctypes.CDLL:
         "khy_totals": [vp, vp],
         "khy_get_flags": [vp, P(ctypes.c_uint), P(ctypes.c_ulonglong), i],
         "khy_profile_steps": [vp, d, l, P(ctypes.c_float)],
+        "khy_step_noalloc": [P(khy_mesh_desc), vp, d, d, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -205,6 +206,15 @@ def khy_profile_steps(h, t_end: float, nsteps: int) -> Tuple[float, float, float
     ms = (ctypes.c_float * 3)()
     _check(lib().khy_profile_steps(h, float(t_end), int(nsteps), ms))
     return ms[0], ms[1], ms[2]
+
+
+def khy_step_noalloc(mesh: Mesh, U_dev_ptr: int, t: float, t_end: float, out_dev_ptr: int,
+                     stream: Optional[int] = None) -> None:
+    """One allocation-free Heun step on a caller-owned device state (raw
+    device pointers: U_dev_ptr holds nvar*ncell doubles, out_dev_ptr 3)."""
+    desc = desc_of(mesh)
+    _check(lib().khy_step_noalloc(ctypes.byref(desc), ctypes.c_void_p(U_dev_ptr), float(t), float(t_end),
+                                  ctypes.c_void_p(out_dev_ptr), ctypes.c_void_p(stream or 0)))
 
 
 def khy_get_time(h) -> Tuple[float, int, float]:
