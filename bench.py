@@ -35,6 +35,25 @@ UNIT = "cell-updates/s"
 BYTES_PER_CELL_UPDATE_3D = 200  # stage 1: read Un, write U1; stage 2: read U1 and Un, write Un+1 (5 x 8 B each)
 
 
+def _recorded_traffic(workload: str):
+    """DRAM bytes (read + write) of the stage-kernel pair from the committed
+    ncu capture, or None when the kernel sources changed since it was taken."""
+    import glob
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "stage_traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for fn in sorted(glob.glob(os.path.join(ROOT, "paper_2501_02317_gb300", "csrc", "*"))):
+            with open(fn, "rb") as f:
+                h.update(f.read())
+        if rec.get("csrc_sha256") != h.hexdigest() or rec.get("workload") != workload:
+            return None
+        return float(rec["stage1_dram_bytes"]) + float(rec["stage2_dram_bytes"])
+    except Exception:
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -275,7 +294,9 @@ def main():
                      "stage_ms": [ms64[1], ms64[2]]},
             "mixed_over_fp64": value / value64,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-                         "frac": achieved / peak_gbs, "traffic": None,
+                         "frac": achieved / peak_gbs,
+                         "traffic": _recorded_traffic("turbulence-3d-%d^3-mixed" % args.n),
+                         "algorithmic_bytes": BYTES_PER_CELL_UPDATE_3D * ncell,
                          "kernel": "stage_kernel (stage 1 + stage 2 of one Heun step)",
                          "bytes_per_cell_update": BYTES_PER_CELL_UPDATE_3D, "stage_ms": [ms[1], ms[2]],
                          "clock_ms": ms[0], "peak_kind": peak_kind},
