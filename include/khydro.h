@@ -148,6 +148,62 @@ khy_status khy_totals(khy_sim *sim, double out[5]);
  * applied) and the number of floor applications; clears them when clear != 0. */
 khy_status khy_get_flags(khy_sim *sim, unsigned *flags, unsigned long long *floor_hits, int clear);
 
+/* ------------------------------------------------------------ many grids */
+
+/* A batch: many independent grids of one dimensionality and one precision,
+ * stepped together (the batched workload; also the engine of the server).
+ * State arrays of a batch are the grids' field-major arrays concatenated in
+ * grid order (count = sum over grids of nvar * ncell).  Every grid keeps its
+ * own clock: its own CFL dt (Sec. 3.1), its own target time and step limit.
+ * One batch step is one Heun step (Sec. 3.3) of every grid that has not
+ * reached its target; finished grids idle.  Each grid's result is bitwise
+ * equal to the same grid stepped alone with khy_step_to. */
+typedef struct khy_batch khy_batch;
+
+/* Validates every descriptor (same ndim and prec for all), allocates the
+ * pooled states and the clocks, binds the stream (NULL: a private stream)
+ * and builds the segment schedule for the tile variant remembered for this
+ * batch shape (variant 0 if none was tuned).  Targets start at t_end = 0, so
+ * nothing steps until khy_batch_set_target. */
+khy_status khy_batch_create(const khy_mesh_desc *descs, int ngrids, void *cuda_stream, khy_batch **out);
+void khy_batch_destroy(khy_batch *b);
+
+/* Host copies of the whole batch state (concatenated, see above).
+ * set_primitive converts on the device as khy_set_primitive does.  Sync. */
+khy_status khy_batch_set_primitive(khy_batch *b, const double *W, size_t count);
+khy_status khy_batch_set_conserved(khy_batch *b, const double *U, size_t count);
+khy_status khy_batch_get_conserved(khy_batch *b, double *U, size_t count);
+
+/* Target time and step limit (counted from now; < 0: none) of one grid, or
+ * of every grid when grid == -1.  Stream-ordered. */
+khy_status khy_batch_set_target(khy_batch *b, int grid, double t_end, long max_steps);
+
+/* Enqueues nsteps batch steps (CUDA graph replays), no host sync. */
+khy_status khy_batch_enqueue_steps(khy_batch *b, long nsteps);
+
+/* Steps until every grid reached its target or step limit; *batch_steps
+ * receives the number of batch steps enqueued.  Synchronises. */
+khy_status khy_batch_run(khy_batch *b, long *batch_steps);
+
+/* Time, steps taken and last dt of one grid.  Synchronises. */
+khy_status khy_batch_get_clock(khy_batch *b, int grid, double *t, long *steps, double *dt);
+
+/* Autotuner: times every tile variant of the batch's dimensionality for
+ * trial_steps steps on the current state (state and clocks are restored
+ * afterwards), keeps the fastest and remembers it for batches of the same
+ * shape (ndim, prec, grid count, cell count).  Synchronises. */
+khy_status khy_batch_autotune(khy_batch *b, int trial_steps, int *variant, float *ms_per_step);
+
+/* Selects a tile variant explicitly (0..2; see khy_batch_info). */
+khy_status khy_batch_set_variant(khy_batch *b, int variant);
+
+/* Like khy_profile_steps for a batch: average ms of the clock, stage-1 and
+ * stage-2 launches over nsteps un-graphed steps. */
+khy_status khy_batch_profile_steps(khy_batch *b, long nsteps, float ms[3]);
+
+/* Total cells, pooled doubles per state, current variant, CTAs of the schedule. */
+khy_status khy_batch_info(khy_batch *b, long long *cells, size_t *pool_doubles, int *variant, int *nblocks);
+
 /* ------------------------------------------------------------ no allocation */
 
 /* Capacity, in bytes, of the stage-1 scratch state that khy_step_noalloc

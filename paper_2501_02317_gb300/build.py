@@ -6,6 +6,7 @@ library:
   * khy_mixed.cu   -- mixed-precision kernels (FP32 flux, FP64 state)
   * khy_runtime.cu -- C ABI, simulation objects, graphs, -fmad=false
   * khy_noalloc.cu -- the allocation-free one-step entry point
+  * khy_batch.cu   -- many grids stepped together (batch engine)
 
 ``python -m paper_2501_02317_gb300.build`` builds; ``build()`` is what
 ``__graft_entry__.build()`` calls.
@@ -33,6 +34,7 @@ UNITS = {
     "khy_mixed": [],
     "khy_runtime": ["-fmad=false"],
     "khy_noalloc": ["-fmad=false"],
+    "khy_batch": ["-fmad=false"],
 }
 
 

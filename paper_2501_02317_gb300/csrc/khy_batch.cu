@@ -1,0 +1,596 @@
+// khy_batch.cu -- many independent grids stepped together (batched and
+// served workloads).
+//
+// All grids of a batch share one dimensionality and one precision.  Their
+// conserved states are concatenated in one device pool (grid i at offset
+// off_i, each grid field-major as in the single-grid API), U^1 in a second
+// pool; every grid has its own clock, so its own dt (Sec. 3.1) and its own
+// target time.  One Heun step of the whole batch is three launches: a clock
+// launch (one thread per grid), and one persistent launch per stage that
+// covers every grid through a precomputed segment schedule (tile runs of
+// planes, balanced by cells over the resident CTAs).  K steps are recorded
+// once in a CUDA graph and replayed.
+//
+// The tile shape is a "variant"; khy_batch_autotune times every variant on
+// the batch's own state and keeps the fastest (cached per batch shape).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/khydro.h"
+#include "khy_internal.h"
+
+using namespace khy;
+
+namespace {
+
+constexpr int kBatchStepsPerGraph = 8;
+
+__global__ void multi_clock_kernel(const GridDesc *grids, Clock *clocks, int ngrids) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ngrids) clock_step(clocks + i, grids[i].g);
+}
+
+__global__ void multi_target_kernel(Clock *clocks, int first, int count, double t_end, long long max_steps) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) {
+        Clock *c = clocks + first + i;
+        c->t_end = t_end;
+        c->max_steps = max_steps < 0 ? LLONG_MAX : c->steps + max_steps;
+        c->active = 0;
+    }
+}
+
+__global__ void multi_wmin_reset_kernel(Clock *clocks, int ngrids) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ngrids) clocks[i].wmin_bits = kInfBits;
+}
+
+// primitive -> conserved for every grid (Eq. 2), one block per grid at a time
+template <int ND>
+__global__ void multi_prim_to_cons_kernel(const GridDesc *grids, int ngrids, const double *W, double *U) {
+    constexpr int NV = ND + 2;
+    for (int gi = blockIdx.x; gi < ngrids; gi += gridDim.x) {
+        const GridDesc &gd = grids[gi];
+        const long long N = gd.g.ncell;
+        const double *w = W + gd.off;
+        double *u = U + gd.off;
+        for (long long c = threadIdx.x; c < N; c += blockDim.x) {
+            const double rho = w[c];
+            double v[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) v[d] = w[(long long)(1 + d) * N + c];
+            const double p = w[(long long)(NV - 1) * N + c];
+            double vsq = v[0] * v[0];
+#pragma unroll
+            for (int d = 1; d < ND; ++d) vsq = vsq + v[d] * v[d];
+            u[c] = rho;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) u[(long long)(1 + d) * N + c] = rho * v[d];
+            u[(long long)(NV - 1) * N + c] = p / gd.g.gm1 + 0.5 * rho * vsq;
+        }
+    }
+}
+
+struct Schedule {
+    std::vector<SegDesc> segs;
+    std::vector<int> cta_seg;  // size nblocks + 1
+    int nblocks = 0;
+};
+
+// Segment schedule for tile shape (TX, TY): every tile of every grid is a run
+// of planes along its march axis; the runs are cut into CTA shares of equal
+// cost (active cells per plane, plus a fixed per-plane cost, plus the four
+// warm-up planes every run pays).
+Schedule build_schedule(const std::vector<GridDesc> &gd, int ndim, int TX, int TY, int resident) {
+    struct TileRun { int grid, x0, y0, nm; double per_plane; };
+    std::vector<TileRun> runs;
+    double total = 0.0;
+    const double fixed = 0.25 * TX * TY;  // barriers, clock and index work per plane
+    for (int i = 0; i < (int)gd.size(); ++i) {
+        const Geom &g = gd[i].g;
+        const int nm = ndim >= 2 ? g.n[ndim - 1] : 1;
+        const int nty = ndim == 3 ? (g.n[1] + TY - 1) / TY : 1;
+        const int ntx = (g.n[0] + TX - 1) / TX;
+        for (int ty = 0; ty < nty; ++ty)
+            for (int tx = 0; tx < ntx; ++tx) {
+                const int w = std::min(TX, g.n[0] - tx * TX);
+                const int h = ndim == 3 ? std::min(TY, g.n[1] - ty * TY) : 1;
+                TileRun r{i, tx * TX, ty * TY, nm, (double)w * h + fixed};
+                runs.push_back(r);
+                total += r.per_plane * (nm + (ndim >= 2 ? 4 : 0));
+            }
+    }
+    Schedule s;
+    const int G = std::max(1, std::min(resident, (int)runs.size() * 64));
+    const double quota = total / G;
+    double acc = 0.0;
+    s.cta_seg.push_back(0);
+    const int min_planes = 8;
+    for (const TileRun &r : runs) {
+        int k = 0;
+        while (k < r.nm) {
+            const double warm = ndim >= 2 ? 4.0 * r.per_plane : 0.0;
+            double room = quota - acc - warm;
+            int take = (int)std::floor(room / r.per_plane);
+            const int left = r.nm - k;
+            if (take >= left || left - take < min_planes) take = left;
+            if (take < std::min(min_planes, left)) {
+                if (acc > 0.0 && (int)s.cta_seg.size() - 1 < G - 1) {  // close this CTA, start the next
+                    s.cta_seg.push_back((int)s.segs.size());
+                    acc = 0.0;
+                    continue;
+                }
+                take = std::min(left, std::max(take, std::min(min_planes, left)));
+            }
+            s.segs.push_back(SegDesc{r.grid, r.x0, r.y0, k, k + take});
+            acc += warm + take * r.per_plane;
+            k += take;
+            if (acc >= quota && (int)s.cta_seg.size() - 1 < G - 1) {
+                s.cta_seg.push_back((int)s.segs.size());
+                acc = 0.0;
+            }
+        }
+    }
+    if (s.cta_seg.back() != (int)s.segs.size()) s.cta_seg.push_back((int)s.segs.size());
+    s.nblocks = (int)s.cta_seg.size() - 1;
+    return s;
+}
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, long long>, int> g_tune_cache;  // (ndim, prec, ngrids, cells) -> variant
+
+}  // namespace
+
+struct khy_batch {
+    int ngrids = 0, ndim = 0, prec = 0, nvar = 0;
+    std::vector<khy_mesh_desc> desc;
+    std::vector<GridDesc> gd;
+    size_t pool = 0;  // doubles per state pool
+    long long cells = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    double *U = nullptr, *U1 = nullptr;
+    GridDesc *d_grids = nullptr;
+    Clock *d_clocks = nullptr;
+    Clock *h_clocks = nullptr;  // pinned
+    SegDesc *d_segs = nullptr;
+    int *d_cta = nullptr;
+    int nblocks = 0;
+    int variant = -1;
+    cudaGraphExec_t graph = nullptr;
+    bool wmin_valid = false;
+};
+
+namespace {
+
+khy_status bfail(int st, const char *msg) { return (khy_status)record_error(st, msg); }
+
+#define KHY_BCUDA(call)                                                                  \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return bfail(e_ == cudaErrorMemoryAllocation ? KHY_ERR_OOM : KHY_ERR_CUDA,   \
+                         cudaGetErrorString(e_));                                        \
+    } while (0)
+
+MultiArgs args_of(const khy_batch *b, int stage) {
+    MultiArgs a;
+    a.grids = b->d_grids;
+    a.segs = b->d_segs;
+    a.cta_seg = b->d_cta;
+    a.clocks = b->d_clocks;
+    if (stage == 1) {
+        a.Uin = b->U;
+        a.Ubase = b->U;
+        a.Uout = b->U1;
+    } else {
+        a.Uin = b->U1;
+        a.Ubase = b->U;
+        a.Uout = b->U;
+    }
+    return a;
+}
+
+khy_status apply_variant(khy_batch *b, int v) {
+    int tx = 0, ty = 0;
+    multi_variant_tile(b->ndim, v, &tx, &ty);
+    if (tx == 0) return bfail(KHY_ERR_ARG, "khy_batch: no such tile variant");
+    const int resident = multi_resident(b->prec == KHY_PREC_FP64, b->ndim, v);
+    if (resident <= 0) return bfail(KHY_ERR_CUDA, "khy_batch: kernel occupancy query failed");
+    Schedule s = build_schedule(b->gd, b->ndim, tx, ty, resident);
+    cudaFree(b->d_segs);
+    cudaFree(b->d_cta);
+    b->d_segs = nullptr;
+    b->d_cta = nullptr;
+    KHY_BCUDA(cudaMalloc(&b->d_segs, sizeof(SegDesc) * std::max<size_t>(1, s.segs.size())));
+    KHY_BCUDA(cudaMalloc(&b->d_cta, sizeof(int) * s.cta_seg.size()));
+    KHY_BCUDA(cudaMemcpyAsync(b->d_segs, s.segs.data(), sizeof(SegDesc) * s.segs.size(), cudaMemcpyHostToDevice,
+                              b->stream));
+    KHY_BCUDA(cudaMemcpyAsync(b->d_cta, s.cta_seg.data(), sizeof(int) * s.cta_seg.size(), cudaMemcpyHostToDevice,
+                              b->stream));
+    KHY_BCUDA(cudaStreamSynchronize(b->stream));
+    b->nblocks = s.nblocks;
+    b->variant = v;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return KHY_OK;
+}
+
+cudaError_t enqueue_batch_step(const khy_batch *b) {
+    multi_clock_kernel<<<(b->ngrids + 127) / 128, 128, 0, b->stream>>>(b->d_grids, b->d_clocks, b->ngrids);
+    cudaError_t e = cudaGetLastError();
+    const bool fp64 = b->prec == KHY_PREC_FP64;
+    if (e == cudaSuccess) e = launch_multi_stage(fp64, args_of(b, 1), b->ndim, b->variant, 1, b->nblocks, b->stream);
+    if (e == cudaSuccess) e = launch_multi_stage(fp64, args_of(b, 2), b->ndim, b->variant, 2, b->nblocks, b->stream);
+    return e;
+}
+
+khy_status ensure_batch_graph(khy_batch *b) {
+    if (b->graph) return KHY_OK;
+    cudaGraph_t g = nullptr;
+    KHY_BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < kBatchStepsPerGraph && err == cudaSuccess; ++i) err = enqueue_batch_step(b);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        KHY_BCUDA(err);
+    }
+    KHY_BCUDA(e2);
+    cudaError_t e3 = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    KHY_BCUDA(e3);
+    return KHY_OK;
+}
+
+khy_status ensure_batch_wmin(khy_batch *b) {
+    if (b->wmin_valid) return KHY_OK;
+    multi_wmin_reset_kernel<<<(b->ngrids + 127) / 128, 128, 0, b->stream>>>(b->d_clocks, b->ngrids);
+    KHY_BCUDA(cudaGetLastError());
+    KHY_BCUDA(launch_multi_dt(b->prec == KHY_PREC_FP64, args_of(b, 1), b->ndim, b->variant, b->nblocks, b->stream));
+    b->wmin_valid = true;
+    return KHY_OK;
+}
+
+khy_status read_clocks(khy_batch *b) {
+    KHY_BCUDA(cudaMemcpyAsync(b->h_clocks, b->d_clocks, sizeof(Clock) * b->ngrids, cudaMemcpyDeviceToHost, b->stream));
+    KHY_BCUDA(cudaStreamSynchronize(b->stream));
+    return KHY_OK;
+}
+
+bool all_done(const khy_batch *b) {
+    for (int i = 0; i < b->ngrids; ++i) {
+        const Clock &c = b->h_clocks[i];
+        if (c.t < c.t_end && c.steps < c.max_steps && !(c.status & FLAG_DT_UNDERFLOW)) return false;
+    }
+    return true;
+}
+
+khy_status batch_status(const khy_batch *b) {
+    for (int i = 0; i < b->ngrids; ++i) {
+        if (b->h_clocks[i].status & FLAG_NONPHYSICAL) return bfail(KHY_ERR_NONPHYSICAL, "khy_batch: non-physical state in a grid");
+        if (b->h_clocks[i].status & FLAG_DT_UNDERFLOW) return bfail(KHY_ERR_DT_UNDERFLOW, "khy_batch: CFL step underflow in a grid");
+    }
+    return KHY_OK;
+}
+
+}  // namespace
+
+namespace khy {
+void multi_variant_tile(int ndim, int variant, int *tx, int *ty) {
+    static const int table[4][kMultiVariants][2] = {
+        {{0, 0}, {0, 0}, {0, 0}}, {{128, 1}, {256, 1}, {0, 0}}, {{64, 1}, {128, 1}, {256, 1}}, {{32, 8}, {32, 16}, {0, 0}}};
+    *tx = *ty = 0;
+    if (ndim < 1 || ndim > 3 || variant < 0 || variant >= kMultiVariants) return;
+    *tx = table[ndim][variant][0];
+    *ty = table[ndim][variant][1];
+}
+int multi_resident(bool fp64, int ndim, int variant) {
+    return fp64 ? multi_resident_fp64(ndim, variant) : multi_resident_mixed(ndim, variant);
+}
+cudaError_t launch_multi_stage(bool fp64, const MultiArgs &a, int ndim, int variant, int stage, int nblocks,
+                               cudaStream_t s) {
+    return fp64 ? launch_multi_stage_fp64(a, ndim, variant, stage, nblocks, s)
+                : launch_multi_stage_mixed(a, ndim, variant, stage, nblocks, s);
+}
+cudaError_t launch_multi_dt(bool fp64, const MultiArgs &a, int ndim, int variant, int nblocks, cudaStream_t s) {
+    return fp64 ? launch_multi_dt_fp64(a, ndim, variant, nblocks, s) : launch_multi_dt_mixed(a, ndim, variant, nblocks, s);
+}
+}  // namespace khy
+
+extern "C" {
+
+khy_status khy_batch_create(const khy_mesh_desc *descs, int ngrids, void *cuda_stream, khy_batch **out) {
+    if (!out) return bfail(KHY_ERR_ARG, "khy_batch_create: out is NULL");
+    *out = nullptr;
+    if (!descs || ngrids < 1) return bfail(KHY_ERR_ARG, "khy_batch_create: need at least one grid");
+    for (int i = 0; i < ngrids; ++i) {
+        int st = validate_desc(&descs[i]);
+        if (st != KHY_OK) return (khy_status)st;
+        if (descs[i].ndim != descs[0].ndim || descs[i].prec != descs[0].prec)
+            return bfail(KHY_ERR_ARG, "khy_batch_create: all grids must share ndim and prec");
+    }
+    khy_batch *b = new (std::nothrow) khy_batch();
+    if (!b) return bfail(KHY_ERR_OOM, "khy_batch_create: host allocation failed");
+    b->ngrids = ngrids;
+    b->ndim = descs[0].ndim;
+    b->prec = descs[0].prec;
+    b->nvar = 2 + b->ndim;
+    b->desc.assign(descs, descs + ngrids);
+    b->gd.resize(ngrids);
+    size_t off = 0;
+    for (int i = 0; i < ngrids; ++i) {
+        GridDesc &g = b->gd[i];
+        memset(&g, 0, sizeof(g));
+        g.g = geom_of_desc(descs[i]);
+        g.off = (long long)off;
+        g.cubic = 1;
+        for (int d = 1; d < b->ndim; ++d)
+            if (g.g.dx[d] != g.g.dx[0]) g.cubic = 0;
+        off += (size_t)b->nvar * (size_t)g.g.ncell;
+        b->cells += g.g.ncell;
+    }
+    b->pool = off;
+    cudaError_t e = cudaSuccess;
+    if (cuda_stream) b->stream = (cudaStream_t)cuda_stream;
+    else {
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        b->own_stream = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->U, sizeof(double) * b->pool);
+    if (e == cudaSuccess) e = cudaMalloc(&b->U1, sizeof(double) * b->pool);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, sizeof(GridDesc) * ngrids);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_clocks, sizeof(Clock) * ngrids);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_clocks, sizeof(Clock) * ngrids);
+    if (e == cudaSuccess) {
+        for (int i = 0; i < ngrids; ++i) {
+            memset(&b->h_clocks[i], 0, sizeof(Clock));
+            b->h_clocks[i].wmin_bits = kInfBits;
+        }
+        e = cudaMemcpyAsync(b->d_clocks, b->h_clocks, sizeof(Clock) * ngrids, cudaMemcpyHostToDevice, b->stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_grids, b->gd.data(), sizeof(GridDesc) * ngrids, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->U, 0, sizeof(double) * b->pool, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        khy_batch_destroy(b);
+        return bfail(e == cudaErrorMemoryAllocation ? KHY_ERR_OOM : KHY_ERR_CUDA, cudaGetErrorString(e));
+    }
+    int v = 0;
+    {  // a previously tuned variant for the same batch shape, else variant 0
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(std::make_tuple(b->ndim, b->prec, ngrids, b->cells));
+        if (it != g_tune_cache.end()) v = it->second;
+    }
+    khy_status st = apply_variant(b, v);
+    if (st != KHY_OK) {
+        khy_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return KHY_OK;
+}
+
+void khy_batch_destroy(khy_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->U);
+    cudaFree(b->U1);
+    cudaFree(b->d_grids);
+    cudaFree(b->d_clocks);
+    cudaFree(b->d_segs);
+    cudaFree(b->d_cta);
+    cudaFreeHost(b->h_clocks);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+khy_status khy_batch_set_primitive(khy_batch *b, const double *W, size_t count) {
+    if (!b || !W) return bfail(KHY_ERR_ARG, "khy_batch_set_primitive: NULL argument");
+    if (count != b->pool) return bfail(KHY_ERR_ARG, "khy_batch_set_primitive: count must be the sum of nvar*ncell");
+    KHY_BCUDA(cudaMemcpyAsync(b->U1, W, sizeof(double) * count, cudaMemcpyHostToDevice, b->stream));
+    const int blocks = std::min(b->ngrids, 152 * 8);
+    switch (b->ndim) {
+        case 1: multi_prim_to_cons_kernel<1><<<blocks, 256, 0, b->stream>>>(b->d_grids, b->ngrids, b->U1, b->U); break;
+        case 2: multi_prim_to_cons_kernel<2><<<blocks, 256, 0, b->stream>>>(b->d_grids, b->ngrids, b->U1, b->U); break;
+        default: multi_prim_to_cons_kernel<3><<<blocks, 256, 0, b->stream>>>(b->d_grids, b->ngrids, b->U1, b->U); break;
+    }
+    KHY_BCUDA(cudaGetLastError());
+    KHY_BCUDA(cudaStreamSynchronize(b->stream));
+    b->wmin_valid = false;
+    return KHY_OK;
+}
+
+khy_status khy_batch_set_conserved(khy_batch *b, const double *U, size_t count) {
+    if (!b || !U) return bfail(KHY_ERR_ARG, "khy_batch_set_conserved: NULL argument");
+    if (count != b->pool) return bfail(KHY_ERR_ARG, "khy_batch_set_conserved: count must be the sum of nvar*ncell");
+    KHY_BCUDA(cudaMemcpyAsync(b->U, U, sizeof(double) * count, cudaMemcpyHostToDevice, b->stream));
+    KHY_BCUDA(cudaStreamSynchronize(b->stream));
+    b->wmin_valid = false;
+    return KHY_OK;
+}
+
+khy_status khy_batch_get_conserved(khy_batch *b, double *U, size_t count) {
+    if (!b || !U) return bfail(KHY_ERR_ARG, "khy_batch_get_conserved: NULL argument");
+    if (count != b->pool) return bfail(KHY_ERR_ARG, "khy_batch_get_conserved: count must be the sum of nvar*ncell");
+    KHY_BCUDA(cudaMemcpyAsync(U, b->U, sizeof(double) * count, cudaMemcpyDeviceToHost, b->stream));
+    KHY_BCUDA(cudaStreamSynchronize(b->stream));
+    return KHY_OK;
+}
+
+khy_status khy_batch_set_target(khy_batch *b, int grid, double t_end, long max_steps) {
+    if (!b) return bfail(KHY_ERR_ARG, "khy_batch_set_target: NULL batch");
+    if (grid < -1 || grid >= b->ngrids) return bfail(KHY_ERR_ARG, "khy_batch_set_target: grid out of range");
+    if (std::isnan(t_end)) return bfail(KHY_ERR_ARG, "khy_batch_set_target: t_end is NaN");
+    const int first = grid < 0 ? 0 : grid, count = grid < 0 ? b->ngrids : 1;
+    multi_target_kernel<<<(count + 127) / 128, 128, 0, b->stream>>>(b->d_clocks, first, count, t_end,
+                                                                     max_steps < 0 ? -1LL : (long long)max_steps);
+    KHY_BCUDA(cudaGetLastError());
+    return KHY_OK;
+}
+
+khy_status khy_batch_enqueue_steps(khy_batch *b, long nsteps) {
+    if (!b) return bfail(KHY_ERR_ARG, "khy_batch_enqueue_steps: NULL batch");
+    if (nsteps < 0) return bfail(KHY_ERR_ARG, "khy_batch_enqueue_steps: nsteps must be >= 0");
+    khy_status st = ensure_batch_wmin(b);
+    if (st != KHY_OK) return st;
+    if ((st = ensure_batch_graph(b)) != KHY_OK) return st;
+    long left = nsteps;
+    for (; left >= kBatchStepsPerGraph; left -= kBatchStepsPerGraph) KHY_BCUDA(cudaGraphLaunch(b->graph, b->stream));
+    for (; left > 0; --left) KHY_BCUDA(enqueue_batch_step(b));
+    return KHY_OK;
+}
+
+khy_status khy_batch_run(khy_batch *b, long *batch_steps) {
+    if (!b) return bfail(KHY_ERR_ARG, "khy_batch_run: NULL batch");
+    long n = 0;
+    khy_status st = read_clocks(b);
+    if (st != KHY_OK) return st;
+    while (!all_done(b)) {
+        if ((st = khy_batch_enqueue_steps(b, kBatchStepsPerGraph)) != KHY_OK) return st;
+        n += kBatchStepsPerGraph;
+        if ((st = read_clocks(b)) != KHY_OK) return st;
+    }
+    if (batch_steps) *batch_steps = n;
+    return batch_status(b);
+}
+
+khy_status khy_batch_get_clock(khy_batch *b, int grid, double *t, long *steps, double *dt) {
+    if (!b || grid < 0 || grid >= b->ngrids) return bfail(KHY_ERR_ARG, "khy_batch_get_clock: bad batch or grid");
+    khy_status st = read_clocks(b);
+    if (st != KHY_OK) return st;
+    if (t) *t = b->h_clocks[grid].t;
+    if (steps) *steps = (long)b->h_clocks[grid].steps;
+    if (dt) *dt = b->h_clocks[grid].dt;
+    return KHY_OK;
+}
+
+khy_status khy_batch_set_variant(khy_batch *b, int variant) {
+    if (!b) return bfail(KHY_ERR_ARG, "khy_batch_set_variant: NULL batch");
+    return apply_variant(b, variant);
+}
+
+khy_status khy_batch_profile_steps(khy_batch *b, long nsteps, float ms[3]) {
+    if (!b || !ms || nsteps < 1) return bfail(KHY_ERR_ARG, "khy_batch_profile_steps: bad argument");
+    khy_status st = ensure_batch_wmin(b);
+    if (st != KHY_OK) return st;
+    cudaEvent_t ev[4];
+    for (auto &x : ev) KHY_BCUDA(cudaEventCreate(&x));
+    double acc[3] = {0, 0, 0};
+    const bool fp64 = b->prec == KHY_PREC_FP64;
+    cudaError_t e = cudaSuccess;
+    for (long i = 0; i < nsteps && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(ev[0], b->stream);
+        if (e == cudaSuccess) {
+            multi_clock_kernel<<<(b->ngrids + 127) / 128, 128, 0, b->stream>>>(b->d_grids, b->d_clocks, b->ngrids);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);
+        if (e == cudaSuccess) e = launch_multi_stage(fp64, args_of(b, 1), b->ndim, b->variant, 1, b->nblocks, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], b->stream);
+        if (e == cudaSuccess) e = launch_multi_stage(fp64, args_of(b, 2), b->ndim, b->variant, 2, b->nblocks, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3], b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            acc[k] += t;
+        }
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    KHY_BCUDA(e);
+    for (int k = 0; k < 3; ++k) ms[k] = (float)(acc[k] / nsteps);
+    return KHY_OK;
+}
+
+khy_status khy_batch_autotune(khy_batch *b, int trial_steps, int *variant, float *ms_per_step) {
+    if (!b) return bfail(KHY_ERR_ARG, "khy_batch_autotune: NULL batch");
+    if (trial_steps < 1) trial_steps = 2;
+    // the trials step a copy; the state and the clocks are put back afterwards
+    double *saved = nullptr;
+    Clock *saved_clk = nullptr;
+    KHY_BCUDA(cudaMalloc(&saved, sizeof(double) * b->pool));
+    cudaError_t e = cudaMalloc(&saved_clk, sizeof(Clock) * b->ngrids);
+    if (e != cudaSuccess) {
+        cudaFree(saved);
+        KHY_BCUDA(e);
+    }
+    e = cudaMemcpyAsync(saved, b->U, sizeof(double) * b->pool, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(saved_clk, b->d_clocks, sizeof(Clock) * b->ngrids, cudaMemcpyDeviceToDevice, b->stream);
+    const int v0 = b->variant;
+    int best = v0;
+    float best_ms = 1e30f;
+    khy_status st = KHY_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int v = 0; v < kMultiVariants && e == cudaSuccess && st == KHY_OK; ++v) {
+        int tx = 0, ty = 0;
+        multi_variant_tile(b->ndim, v, &tx, &ty);
+        if (tx == 0) continue;
+        if ((st = apply_variant(b, v)) != KHY_OK) break;
+        multi_target_kernel<<<(b->ngrids + 127) / 128, 128, 0, b->stream>>>(b->d_clocks, 0, b->ngrids, INFINITY,
+                                                                             (long long)trial_steps + 1);
+        b->wmin_valid = false;
+        if ((st = ensure_batch_wmin(b)) != KHY_OK) break;
+        e = enqueue_batch_step(b);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        for (int i = 0; i < trial_steps && e == cudaSuccess; ++i) e = enqueue_batch_step(b);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        ms /= trial_steps;
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+        // restore the state for the next trial
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->U, saved, sizeof(double) * b->pool, cudaMemcpyDeviceToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_clocks, saved_clk, sizeof(Clock) * b->ngrids, cudaMemcpyDeviceToDevice, b->stream);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(b->stream);
+    cudaFree(saved);
+    cudaFree(saved_clk);
+    b->wmin_valid = false;
+    if (st != KHY_OK) return st;
+    KHY_BCUDA(e);
+    if ((st = apply_variant(b, best)) != KHY_OK) return st;
+    (void)v0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[std::make_tuple(b->ndim, b->prec, b->ngrids, b->cells)] = best;
+    }
+    if (variant) *variant = best;
+    if (ms_per_step) *ms_per_step = best_ms;
+    return KHY_OK;
+}
+
+khy_status khy_batch_info(khy_batch *b, long long *cells, size_t *pool_doubles, int *variant, int *nblocks) {
+    if (!b) return bfail(KHY_ERR_ARG, "khy_batch_info: NULL batch");
+    if (cells) *cells = b->cells;
+    if (pool_doubles) *pool_doubles = b->pool;
+    if (variant) *variant = b->variant;
+    if (nblocks) *nblocks = b->nblocks;
+    return KHY_OK;
+}
+
+}  // extern "C"

@@ -15,4 +15,15 @@ cudaError_t launch_dt_fp64(const Geom &g, const double *U, Clock *clk, cudaStrea
 
 cudaError_t prepare_fp64(int ndim) { return prepare_prec<double>(ndim); }
 
+cudaError_t launch_multi_stage_fp64(const MultiArgs &a, int ndim, int variant, int stage, int nblocks,
+                                  cudaStream_t s) {
+    return launch_multi_stage_prec<double>(a, ndim, variant, stage, nblocks, s);
+}
+
+cudaError_t launch_multi_dt_fp64(const MultiArgs &a, int ndim, int variant, int nblocks, cudaStream_t s) {
+    return launch_multi_dt_prec<double>(a, ndim, variant, nblocks, s);
+}
+
+int multi_resident_fp64(int ndim, int variant) { return multi_resident_prec<double>(ndim, variant); }
+
 }  // namespace khy

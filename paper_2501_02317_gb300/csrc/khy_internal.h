@@ -16,6 +16,23 @@ cudaError_t launch_dt_fp64(const Geom &g, const double *U, Clock *clk, cudaStrea
 cudaError_t launch_stage_mixed(const StageArgs &a, int stage, cudaStream_t s);
 cudaError_t launch_dt_mixed(const Geom &g, const double *U, Clock *clk, cudaStream_t s);
 
+// Many-grid (batched / served) launches.  A variant is a tile shape; the
+// variants of each dimensionality are listed by multi_variant_tile (the
+// autotuner times them and picks one).  nblocks is the CTA count of the
+// segment schedule (at most multi_resident).
+constexpr int kMultiVariants = 3;
+void multi_variant_tile(int ndim, int variant, int *tx, int *ty);  // tx = 0: no such variant
+int multi_resident(bool fp64, int ndim, int variant);              // resident CTAs, 0 on error
+cudaError_t launch_multi_stage(bool fp64, const MultiArgs &a, int ndim, int variant, int stage, int nblocks,
+                               cudaStream_t s);
+cudaError_t launch_multi_dt(bool fp64, const MultiArgs &a, int ndim, int variant, int nblocks, cudaStream_t s);
+cudaError_t launch_multi_stage_fp64(const MultiArgs &a, int ndim, int variant, int stage, int nblocks, cudaStream_t s);
+cudaError_t launch_multi_stage_mixed(const MultiArgs &a, int ndim, int variant, int stage, int nblocks, cudaStream_t s);
+cudaError_t launch_multi_dt_fp64(const MultiArgs &a, int ndim, int variant, int nblocks, cudaStream_t s);
+cudaError_t launch_multi_dt_mixed(const MultiArgs &a, int ndim, int variant, int nblocks, cudaStream_t s);
+int multi_resident_fp64(int ndim, int variant);
+int multi_resident_mixed(int ndim, int variant);
+
 // Sets the shared-memory limits of the stage kernels of one dimensionality
 // and caches their persistent grid sizes; call before the first launch (in
 // particular before a stream capture).

@@ -51,6 +51,39 @@ struct Clock {
 
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
 
+// Start of a Heun step for one grid (Sec. 3.1: dt on the first sub-step
+// only): dt = C * (accumulated CFL minimum), clipped so the step lands on
+// t_end; advances t and the step counter, arms the stage kernels and resets
+// the minimum for the stage-2 launch.  Inactive once t >= t_end, the step
+// limit is reached or dt underflowed.
+__device__ __forceinline__ void clock_step(Clock *c, const Geom &g) {
+    if (!(c->t < c->t_end) || c->steps >= c->max_steps || (c->status & FLAG_DT_UNDERFLOW)) {
+        c->active = 0;
+        return;
+    }
+    const double w = __longlong_as_double((long long)c->wmin_bits);
+    double dt = g.cfl * w;
+    int last = 0;
+    const double rem = c->t_end - c->t;
+    if (dt >= rem) {
+        dt = rem;
+        last = 1;
+    }
+    if (!(dt > 1e-300) || !(dt < INFINITY)) {
+        c->status |= FLAG_DT_UNDERFLOW;
+        c->active = 0;
+        return;
+    }
+    c->dt = dt;
+    c->dtdx[0] = dt / g.dx[0];
+    c->dtdx[1] = dt / g.dx[1];
+    c->dtdx[2] = dt / g.dx[2];
+    c->t = last ? c->t_end : c->t + dt;
+    c->steps += 1;
+    c->active = 1;
+    c->wmin_bits = kInfBits;
+}
+
 // ------------------------------------------------------------ Sec. 3.1.1
 // Maps coordinate x (possibly a ghost) onto an interior index along an axis
 // with n cells and boundary rules (lo, hi).  *act receives the velocity rule

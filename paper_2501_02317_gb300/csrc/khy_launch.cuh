@@ -82,6 +82,113 @@ static cudaError_t prepare_prec(int ndim) {
     }
 }
 
+// ---------------------------------------------------------------- many grids
+
+template <class R, int ND, int STAGE, int TX, int TY>
+struct MultiLaunch {
+    static int &resident() {
+        static int r = 0;
+        return r;
+    }
+    static cudaError_t prepare() {
+        constexpr size_t smem = Tile<ND, TX, TY>::template smem_bytes<R>();
+        auto kern = multi_stage_kernel<R, ND, STAGE, TX, TY>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, smem)) != cudaSuccess) return e;
+        resident() = sms * (per_sm > 0 ? per_sm : 1);
+        return cudaSuccess;
+    }
+    static cudaError_t launch(const MultiArgs &a, int nblocks, cudaStream_t s) {
+        if (resident() == 0) {
+            cudaError_t e = prepare();
+            if (e != cudaSuccess) return e;
+        }
+        constexpr size_t smem = Tile<ND, TX, TY>::template smem_bytes<R>();
+        if (nblocks <= 0) return cudaSuccess;
+        multi_stage_kernel<R, ND, STAGE, TX, TY><<<nblocks, TX * TY, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+};
+
+// variant table: tile shapes per dimensionality
+struct VariantTile { int tx, ty; };
+__host__ __device__ constexpr VariantTile variant_tile(int ndim, int v) {
+    return ndim == 1 ? (v == 0 ? VariantTile{128, 1} : v == 1 ? VariantTile{256, 1} : VariantTile{0, 0})
+         : ndim == 2 ? (v == 0 ? VariantTile{64, 1} : v == 1 ? VariantTile{128, 1} : v == 2 ? VariantTile{256, 1} : VariantTile{0, 0})
+         : ndim == 3 ? (v == 0 ? VariantTile{32, 8} : v == 1 ? VariantTile{32, 16} : VariantTile{0, 0})
+                     : VariantTile{0, 0};
+}
+
+template <int ND, int V>
+struct VT {
+    static constexpr int tx = (variant_tile(ND, V).tx > 0) ? variant_tile(ND, V).tx : 32;
+    static constexpr int ty = (variant_tile(ND, V).tx > 0) ? variant_tile(ND, V).ty : 1;
+};
+
+template <class R, int ND, int V, int STAGE>
+using MultiOf = MultiLaunch<R, ND, STAGE, VT<ND, V>::tx, VT<ND, V>::ty>;
+
+template <class R, int ND, int V>
+static cudaError_t multi_stage_v(const MultiArgs &a, int stage, int nblocks, cudaStream_t s) {
+    return stage == 1 ? MultiOf<R, ND, V, 1>::launch(a, nblocks, s) : MultiOf<R, ND, V, 2>::launch(a, nblocks, s);
+}
+
+template <class R>
+static cudaError_t launch_multi_stage_prec(const MultiArgs &a, int ndim, int v, int stage, int nblocks, cudaStream_t s) {
+    if (variant_tile(ndim, v).tx == 0) return cudaErrorInvalidValue;
+    switch (ndim * 10 + v) {
+        case 10: return multi_stage_v<R, 1, 0>(a, stage, nblocks, s);
+        case 11: return multi_stage_v<R, 1, 1>(a, stage, nblocks, s);
+        case 20: return multi_stage_v<R, 2, 0>(a, stage, nblocks, s);
+        case 21: return multi_stage_v<R, 2, 1>(a, stage, nblocks, s);
+        case 22: return multi_stage_v<R, 2, 2>(a, stage, nblocks, s);
+        case 30: return multi_stage_v<R, 3, 0>(a, stage, nblocks, s);
+        case 31: return multi_stage_v<R, 3, 1>(a, stage, nblocks, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class R, int ND, int V>
+static int multi_resident_v() {
+    using L1 = MultiOf<R, ND, V, 1>;
+    using L2 = MultiOf<R, ND, V, 2>;
+    if (L1::resident() == 0 && L1::prepare() != cudaSuccess) return 0;
+    if (L2::resident() == 0 && L2::prepare() != cudaSuccess) return 0;
+    return L1::resident() < L2::resident() ? L1::resident() : L2::resident();
+}
+
+template <class R>
+static int multi_resident_prec(int ndim, int v) {
+    switch (ndim * 10 + v) {
+        case 10: return multi_resident_v<R, 1, 0>();
+        case 11: return multi_resident_v<R, 1, 1>();
+        case 20: return multi_resident_v<R, 2, 0>();
+        case 21: return multi_resident_v<R, 2, 1>();
+        case 22: return multi_resident_v<R, 2, 2>();
+        case 30: return multi_resident_v<R, 3, 0>();
+        case 31: return multi_resident_v<R, 3, 1>();
+        default: return 0;
+    }
+}
+
+template <class R>
+static cudaError_t launch_multi_dt_prec(const MultiArgs &a, int ndim, int v, int nblocks, cudaStream_t s) {
+    const VariantTile t = variant_tile(ndim, v);
+    if (t.tx == 0) return cudaErrorInvalidValue;
+    if (nblocks <= 0) return cudaSuccess;
+    switch (ndim) {
+        case 1: multi_dt_kernel<R, 1><<<nblocks, 256, 0, s>>>(a, t.tx, t.ty); break;
+        case 2: multi_dt_kernel<R, 2><<<nblocks, 256, 0, s>>>(a, t.tx, t.ty); break;
+        case 3: multi_dt_kernel<R, 3><<<nblocks, 256, 0, s>>>(a, t.tx, t.ty); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <class R>
 static cudaError_t launch_dt_prec(const Geom &g, const double *U, Clock *clk, cudaStream_t s) {
     const long long blocks_needed = (g.ncell + 255) / 256;

@@ -16,4 +16,15 @@ cudaError_t launch_dt_mixed(const Geom &g, const double *U, Clock *clk, cudaStre
 
 cudaError_t prepare_mixed(int ndim) { return prepare_prec<float>(ndim); }
 
+cudaError_t launch_multi_stage_mixed(const MultiArgs &a, int ndim, int variant, int stage, int nblocks,
+                                  cudaStream_t s) {
+    return launch_multi_stage_prec<float>(a, ndim, variant, stage, nblocks, s);
+}
+
+cudaError_t launch_multi_dt_mixed(const MultiArgs &a, int ndim, int variant, int nblocks, cudaStream_t s) {
+    return launch_multi_dt_prec<float>(a, ndim, variant, nblocks, s);
+}
+
+int multi_resident_mixed(int ndim, int variant) { return multi_resident_prec<float>(ndim, variant); }
+
 }  // namespace khy

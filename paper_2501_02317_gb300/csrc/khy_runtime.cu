@@ -49,33 +49,7 @@ constexpr int kStepsPerGraph = 16;
 // Start of a Heun step: dt from the accumulated CFL minimum, clipped to
 // t_end (Sec. 3.1, first sub-step only); advances t and the step counter and
 // arms the stage kernels; resets the minimum for the stage-2 launch.
-__global__ void clock_step_kernel(Clock *c, Geom g) {
-    if (!(c->t < c->t_end) || c->steps >= c->max_steps || (c->status & FLAG_DT_UNDERFLOW)) {
-        c->active = 0;
-        return;
-    }
-    const double w = __longlong_as_double((long long)c->wmin_bits);
-    double dt = g.cfl * w;
-    int last = 0;
-    const double rem = c->t_end - c->t;
-    if (dt >= rem) {
-        dt = rem;
-        last = 1;
-    }
-    if (!(dt > 1e-300) || !(dt < INFINITY)) {
-        c->status |= FLAG_DT_UNDERFLOW;
-        c->active = 0;
-        return;
-    }
-    c->dt = dt;
-    c->dtdx[0] = dt / g.dx[0];
-    c->dtdx[1] = dt / g.dx[1];
-    c->dtdx[2] = dt / g.dx[2];
-    c->t = last ? c->t_end : c->t + dt;
-    c->steps += 1;
-    c->active = 1;
-    c->wmin_bits = kInfBits;
-}
+__global__ void clock_step_kernel(Clock *c, Geom g) { clock_step(c, g); }
 
 __global__ void clock_target_kernel(Clock *c, double t_end, long long max_steps) {
     c->t_end = t_end;

@@ -65,38 +65,24 @@ struct Tile {
     }
 };
 
+// One segment: tile (x0, y0) of one grid, planes [k0, k1) of its march axis.
+// Shared by the single-grid and the multi-grid kernels.  Accumulates the
+// status bits, the floor count and (stage 2) the CFL minimum into the
+// caller's registers.
 template <class R, int ND, int STAGE, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) stage_kernel(StageArgs a) {
+__device__ __forceinline__ void run_segment(const Geom &g, const double *__restrict__ Uin, const double *Ubase,
+                                            double *Uout, const double (&dtdx)[3], int cubic, int x0, int y0,
+                                            int k0, int k1, R *sW, R *sFx, R *sFy, unsigned &flags,
+                                            unsigned &floors, double &wmin) {
     constexpr bool MIX = std::is_same<R, float>::value;
     using T = Tile<ND, TX, TY>;
     constexpr int NV = T::NV, PX = T::PX, PC = T::PC, NT = T::NT;
     constexpr int DM = ND - 1;  // march axis (ND >= 2)
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *sW = reinterpret_cast<R *>(smem_raw);   // [NSLOT][NV][PC] primitives
-    R *sFx = sW + (size_t)T::NSLOT * NV * PC;  // [NV][TY][TX+1] x-face fluxes
-    R *sFy = sFx + (size_t)NV * T::NXF;        // [NV][TY+1][TX] y-face fluxes (3D)
-
-    const Geom &g = a.g;
-    const Clock *clk = a.clk;
-    if (!clk->active) return;
-    const double dtdx[3] = {clk->dtdx[0], clk->dtdx[1], clk->dtdx[2]};
     const Consts<R> kc = make_consts<R>(g);
     const mx::MixConsts mk = mx::make_mix(g);
     const long long N = g.ncell;
-
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int ntx = (g.n[0] + TX - 1) / TX;
-    const int nty = (ND == 3) ? (g.n[1] + TY - 1) / TY : 1;
-    const int nm = (ND >= 2) ? g.n[DM] : 1;
-    const long long total = (long long)ntx * nty * nm;
-    const long long s0 = total * blockIdx.x / gridDim.x;
-    const long long s1 = total * (blockIdx.x + 1) / gridDim.x;
-
-    unsigned flags = 0, floors = 0;
-    double wmin = __longlong_as_double((long long)kInfBits);
-
-    int x0 = 0, y0 = 0, k0 = 0, k1 = 0;  // current tile origin and plane range
 
     // plane L of the march axis (ignored in 1D) -> ring slot
     auto load_plane = [&](int L, int slot) {
@@ -116,7 +102,7 @@ __global__ void __launch_bounds__(TX *TY) stage_kernel(StageArgs a) {
             double u[NV];
             R w[NV];
 #pragma unroll
-            for (int q = 0; q < NV; ++q) u[q] = __ldg(a.Uin + (long long)q * N + idx);
+            for (int q = 0; q < NV; ++q) u[q] = __ldg(Uin + (long long)q * N + idx);
             unsigned fl = 0;
             if constexpr (MIX) {
                 mx::recover<ND>(u, mk, w, flags, fl);
@@ -181,7 +167,7 @@ __global__ void __launch_bounds__(TX *TY) stage_kernel(StageArgs a) {
         for (int q = 0; q < NV; ++q) {
             const R *fx = sFx + (size_t)q * T::NXF + ty * (TX + 1) + tx;
             const R *fy = sFy + (size_t)q * T::NYF + ty * TX + tx;
-            const double u = a.Uin[(long long)q * N + idx];
+            const double u = Uin[(long long)q * N + idx];
             double r;
             if constexpr (!MIX) {
                 // dU = -sum_d (dt/dx_d)(F_hi - F_lo), directions in x, y, z order
@@ -189,14 +175,14 @@ __global__ void __launch_bounds__(TX *TY) stage_kernel(StageArgs a) {
                 if (ND == 3) acc = acc - dtdx[1] * (fy[TX] - fy[0]);
                 if (ND >= 2) acc = acc - dtdx[DM] * (Fmhi[q] - Fmlo[q]);
                 if (STAGE == 1) r = u + acc;
-                else r = 0.5 * (a.Ubase[(long long)q * N + idx] + (u + acc));
+                else r = 0.5 * (Ubase[(long long)q * N + idx] + (u + acc));
             } else {
                 // F_lo - F_hi per direction, exact as float-float pairs
                 const mx::FF Dx = mx::two_sum(fx[0], -fx[1]);
                 mx::FF Dy = {0.f, 0.f}, Dm = {0.f, 0.f};
                 if (ND == 3) Dy = mx::two_sum(fy[0], -fy[TX]);
                 if (ND >= 2) Dm = mx::two_sum(Fmlo[q], -Fmhi[q]);
-                if (a.cubic) {
+                if (cubic) {
                     mx::FF S = Dx;
                     if (ND == 3) S = mx::ff_add(S, Dy);
                     if (ND >= 2) S = mx::ff_add(S, Dm);
@@ -207,7 +193,7 @@ __global__ void __launch_bounds__(TX *TY) stage_kernel(StageArgs a) {
                     } else {
                         const double hc = 0.5 * c;
                         const double lo = mx::f2d(__fmul_rn(mx::d2f(hc), S.lo));
-                        const double A = __dadd_rn(a.Ubase[(long long)q * N + idx], u);
+                        const double A = __dadd_rn(Ubase[(long long)q * N + idx], u);
                         r = __fma_rn(hc, mx::f2d(S.hi), __fma_rn(0.5, A, lo));
                     }
                 } else {
@@ -215,11 +201,11 @@ __global__ void __launch_bounds__(TX *TY) stage_kernel(StageArgs a) {
                     if (ND == 3) acc = __fma_rn(dtdx[1], mx::f2d(Dy.hi), __fma_rn(dtdx[1], mx::f2d(Dy.lo), acc));
                     if (ND >= 2) acc = __fma_rn(dtdx[DM], mx::f2d(Dm.hi), __fma_rn(dtdx[DM], mx::f2d(Dm.lo), acc));
                     if (STAGE == 1) r = __dadd_rn(u, acc);
-                    else r = __dmul_rn(0.5, __dadd_rn(a.Ubase[(long long)q * N + idx], __dadd_rn(u, acc)));
+                    else r = __dmul_rn(0.5, __dadd_rn(Ubase[(long long)q * N + idx], __dadd_rn(u, acc)));
                 }
             }
             un[q] = r;
-            a.Uout[(long long)q * N + idx] = r;
+            Uout[(long long)q * N + idx] = r;
         }
         if (STAGE == 2) {  // CFL candidate of the new state for the next step
             double c;
@@ -235,57 +221,55 @@ __global__ void __launch_bounds__(TX *TY) stage_kernel(StageArgs a) {
         }
     };
 
-    for (long long pos = s0; pos < s1;) {
-        const long long tile = pos / nm;
-        k0 = (int)(pos % nm);
-        k1 = (int)((long long)nm < k0 + (s1 - pos) ? (long long)nm : k0 + (s1 - pos));
-        x0 = (int)(tile % ntx) * TX;
-        y0 = (ND == 3) ? (int)(tile / ntx) * TY : 0;
-        pos += k1 - k0;
-        if (ND == 1) {
-            load_plane(0, 0);
-            __syncthreads();
-            inplane_faces(0);
-            __syncthreads();
-            R dummy[NV];
-            update_cell(0, dummy, dummy);
-            __syncthreads();
-        } else {
-            R Fmlo[NV], Fmhi[NV];
+    if (ND == 1) {
+        load_plane(0, 0);
+        __syncthreads();
+        inplane_faces(0);
+        __syncthreads();
+        R dummy[NV];
+        update_cell(0, dummy, dummy);
+        __syncthreads();
+    } else {
+        R Fmlo[NV], Fmhi[NV];
 #pragma unroll
-            for (int q = 0; q < NV; ++q) { Fmlo[q] = R(0); Fmhi[q] = R(0); }
-            for (int L = k0 - 2; L <= k1 + 1; ++L) {
-                load_plane(L, L & 3);
-                __syncthreads();
-                if (L >= k0 + 1) {
-                    const int cur = L - 2;
-                    {   // march-axis face between cur and cur+1, from planes cur-1 .. cur+2
-                        R s[4][NV];
-                        const int e = (ND == 3) ? (ty + 2) * PX + tx + 2 : tx + 2;
+        for (int q = 0; q < NV; ++q) { Fmlo[q] = R(0); Fmhi[q] = R(0); }
+        for (int L = k0 - 2; L <= k1 + 1; ++L) {
+            load_plane(L, L & 3);
+            __syncthreads();
+            if (L >= k0 + 1) {
+                const int cur = L - 2;
+                {   // march-axis face between cur and cur+1, from planes cur-1 .. cur+2
+                    R s[4][NV];
+                    const int e = (ND == 3) ? (ty + 2) * PX + tx + 2 : tx + 2;
 #pragma unroll
-                        for (int o = 0; o < 4; ++o) {
-                            const R *pl = sW + (size_t)((cur - 1 + o) & 3) * NV * PC;
+                    for (int o = 0; o < 4; ++o) {
+                        const R *pl = sW + (size_t)((cur - 1 + o) & 3) * NV * PC;
 #pragma unroll
-                            for (int q = 0; q < NV; ++q) s[o][q] = pl[(size_t)q * PC + e];
-                        }
-                        face_flux<ND, R>(s, DM, kc, Fmhi);
+                        for (int q = 0; q < NV; ++q) s[o][q] = pl[(size_t)q * PC + e];
                     }
-                    if (cur >= k0) inplane_faces(cur & 3);
-                    __syncthreads();
-                    if (cur >= k0) update_cell(cur, Fmlo, Fmhi);
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) Fmlo[q] = Fmhi[q];
-                } else {
-                    __syncthreads();
+                    face_flux<ND, R>(s, DM, kc, Fmhi);
                 }
+                if (cur >= k0) inplane_faces(cur & 3);
+                __syncthreads();
+                if (cur >= k0) update_cell(cur, Fmlo, Fmhi);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) Fmlo[q] = Fmhi[q];
+            } else {
+                __syncthreads();
             }
         }
     }
+}
 
-    // block reductions: status bits, floor count, CFL minimum
+// Block-wide reduction of the status bits, floor count and (stage 2) CFL
+// minimum into one clock.  Every thread of the block must call it.
+template <int STAGE, int NT>
+__device__ __forceinline__ void reduce_to_clock(Clock *clk, unsigned flags, unsigned floors, double wmin) {
     __shared__ unsigned s_flags;
     __shared__ unsigned long long s_floors;
     __shared__ double s_wmin[32];
+    const int tid = threadIdx.x;
+    __syncthreads();
     if (tid == 0) { s_flags = 0; s_floors = 0; }
     __syncthreads();
     const unsigned wf = __reduce_or_sync(0xffffffffu, flags);
@@ -303,13 +287,148 @@ __global__ void __launch_bounds__(TX *TY) stage_kernel(StageArgs a) {
     }
     __syncthreads();
     if (tid == 0) {
-        if (s_flags) atomicOr(&a.clk->status, s_flags);
-        if (s_floors) atomicAdd(&a.clk->floor_hits, s_floors);
+        if (s_flags) atomicOr(&clk->status, s_flags);
+        if (s_floors) atomicAdd(&clk->floor_hits, s_floors);
         if (STAGE == 2) {
             double m = s_wmin[0];
             for (int i = 1; i < NT / 32; ++i) m = s_wmin[i] < m ? s_wmin[i] : m;
-            atomicMin(&a.clk->wmin_bits, (unsigned long long)__double_as_longlong(m));
+            if (m < __longlong_as_double((long long)kInfBits))
+                atomicMin(&clk->wmin_bits, (unsigned long long)__double_as_longlong(m));
         }
+    }
+}
+
+template <class R, int ND, int STAGE, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) stage_kernel(StageArgs a) {
+    using T = Tile<ND, TX, TY>;
+    constexpr int NV = T::NV, PC = T::PC, NT = T::NT;
+    constexpr int DM = ND - 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sW = reinterpret_cast<R *>(smem_raw);   // [NSLOT][NV][PC] primitives
+    R *sFx = sW + (size_t)T::NSLOT * NV * PC;  // [NV][TY][TX+1] x-face fluxes
+    R *sFy = sFx + (size_t)NV * T::NXF;        // [NV][TY+1][TX] y-face fluxes (3D)
+
+    const Geom &g = a.g;
+    const Clock *clk = a.clk;
+    if (!clk->active) return;
+    const double dtdx[3] = {clk->dtdx[0], clk->dtdx[1], clk->dtdx[2]};
+
+    const int ntx = (g.n[0] + TX - 1) / TX;
+    const int nty = (ND == 3) ? (g.n[1] + TY - 1) / TY : 1;
+    const int nm = (ND >= 2) ? g.n[DM] : 1;
+    const long long total = (long long)ntx * nty * nm;
+    const long long s0 = total * blockIdx.x / gridDim.x;
+    const long long s1 = total * (blockIdx.x + 1) / gridDim.x;
+
+    unsigned flags = 0, floors = 0;
+    double wmin = __longlong_as_double((long long)kInfBits);
+    for (long long pos = s0; pos < s1;) {
+        const long long tile = pos / nm;
+        const int k0 = (int)(pos % nm);
+        const int k1 = (int)((long long)nm < k0 + (s1 - pos) ? (long long)nm : k0 + (s1 - pos));
+        const int x0 = (int)(tile % ntx) * TX;
+        const int y0 = (ND == 3) ? (int)(tile / ntx) * TY : 0;
+        pos += k1 - k0;
+        run_segment<R, ND, STAGE, TX, TY>(g, a.Uin, a.Ubase, a.Uout, dtdx, a.cubic, x0, y0, k0, k1, sW, sFx, sFy,
+                                          flags, floors, wmin);
+    }
+    reduce_to_clock<STAGE, NT>(a.clk, flags, floors, wmin);
+}
+
+// ---------------------------------------------------------------- many grids
+// Batched and served workloads: many independent grids (one dimensionality,
+// one precision) in one pooled state, each with its own clock and dt.  One
+// launch per stage covers all grids; CTA b runs its precomputed list of
+// segments (tile runs), balanced by cells on the host.
+
+struct GridDesc {
+    Geom g;
+    long long off;  // offset (in doubles) of the grid's state in the pools
+    int cubic;
+    int pad;
+};
+
+struct SegDesc {
+    int grid;
+    int x0, y0;  // tile origin
+    int k0, k1;  // march-axis planes [k0, k1)
+};
+
+struct MultiArgs {
+    const GridDesc *grids;
+    const SegDesc *segs;
+    const int *cta_seg;  // CTA b runs segments [cta_seg[b], cta_seg[b + 1])
+    const double *Uin;   // pool the fluxes are computed from (U or U1)
+    const double *Ubase; // U pool (stage 2 average)
+    double *Uout;        // U1 pool (stage 1) or U pool (stage 2)
+    Clock *clocks;       // one per grid
+};
+
+template <class R, int ND, int STAGE, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) multi_stage_kernel(MultiArgs a) {
+    using T = Tile<ND, TX, TY>;
+    constexpr int NV = T::NV, PC = T::PC, NT = T::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sW = reinterpret_cast<R *>(smem_raw);
+    R *sFx = sW + (size_t)T::NSLOT * NV * PC;
+    R *sFy = sFx + (size_t)NV * T::NXF;
+    const int sb = a.cta_seg[blockIdx.x], se = a.cta_seg[blockIdx.x + 1];
+    for (int si = sb; si < se; ++si) {
+        const SegDesc sd = a.segs[si];
+        Clock *clk = a.clocks + sd.grid;
+        if (!clk->active) continue;  // same value for every thread of the CTA
+        const GridDesc *gd = a.grids + sd.grid;
+        const Geom g = gd->g;
+        const double dtdx[3] = {clk->dtdx[0], clk->dtdx[1], clk->dtdx[2]};
+        unsigned flags = 0, floors = 0;
+        double wmin = __longlong_as_double((long long)kInfBits);
+        run_segment<R, ND, STAGE, TX, TY>(g, a.Uin + gd->off, a.Ubase + gd->off, a.Uout + gd->off, dtdx, gd->cubic,
+                                          sd.x0, sd.y0, sd.k0, sd.k1, sW, sFx, sFy, flags, floors, wmin);
+        reduce_to_clock<STAGE, NT>(clk, flags, floors, wmin);
+    }
+}
+
+// Per-grid CFL minimum of every grid over the same segments (after the
+// states were set from outside).
+template <class R, int ND>
+__global__ void __launch_bounds__(256) multi_dt_kernel(MultiArgs a, int TX, int TY) {
+    constexpr bool MIX = std::is_same<R, float>::value;
+    constexpr int NV = ND + 2;
+    const int sb = a.cta_seg[blockIdx.x], se = a.cta_seg[blockIdx.x + 1];
+    for (int si = sb; si < se; ++si) {
+        const SegDesc sd = a.segs[si];
+        const GridDesc *gd = a.grids + sd.grid;
+        const Geom g = gd->g;
+        const mx::MixConsts mk = mx::make_mix(g);
+        const long long N = g.ncell;
+        const double *U = a.Uin + gd->off;
+        const int w = min(TX, g.n[0] - sd.x0);
+        const int h = (ND == 3) ? min(TY, g.n[1] - sd.y0) : 1;
+        const long long cnt = (long long)w * h * (sd.k1 - sd.k0);
+        unsigned flags = 0, floors = 0;
+        double wmin = __longlong_as_double((long long)kInfBits);
+        for (long long i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const int cx = sd.x0 + (int)(i % w);
+            const int cy = (ND == 3) ? sd.y0 + (int)((i / w) % h) : 0;
+            const int cm = sd.k0 + (int)(i / ((long long)w * h));
+            const long long c = (ND == 3) ? ((long long)cm * g.n[1] + cy) * g.n[0] + cx
+                                          : (ND == 2 ? (long long)cm * g.n[0] + cx : (long long)cx);
+            double u[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) u[q] = U[(long long)q * N + c];
+            double m;
+            if constexpr (MIX) {
+                float wv[NV];
+                mx::recover<ND>(u, mk, wv, flags, floors);
+                m = mx::f2d(mx::cfl_candidate<ND>(u, mk));
+            } else {
+                double wv[NV];
+                recover<ND>(u, g, wv, flags, floors);
+                m = cfl_candidate<ND>(wv, g);
+            }
+            wmin = m < wmin ? m : wmin;
+        }
+        reduce_to_clock<2, 256>(a.clocks + sd.grid, flags, 0u, wmin);
     }
 }
 

@@ -33,6 +33,10 @@ EXPORTS = [
     "khy_set_conserved_dev", "khy_set_primitive_dev", "khy_set_time", "khy_step_to",
     "khy_enqueue_steps", "khy_get_conserved", "khy_get_conserved_dev", "khy_get_time", "khy_totals",
     "khy_get_flags", "khy_last_error", "khy_version", "khy_profile_steps", "khy_step_noalloc",
+    "khy_batch_create", "khy_batch_destroy", "khy_batch_set_primitive", "khy_batch_set_conserved",
+    "khy_batch_get_conserved", "khy_batch_set_target", "khy_batch_enqueue_steps", "khy_batch_run",
+    "khy_batch_get_clock", "khy_batch_autotune", "khy_batch_set_variant", "khy_batch_profile_steps",
+    "khy_batch_info",
 ]
 
 
@@ -105,6 +109,18 @@ def lib() -> ctypes.CDLL:
         "khy_get_flags": [vp, P(ctypes.c_uint), P(ctypes.c_ulonglong), i],
         "khy_profile_steps": [vp, d, l, P(ctypes.c_float)],
         "khy_step_noalloc": [P(khy_mesh_desc), vp, d, d, vp, vp],
+        "khy_batch_create": [P(khy_mesh_desc), i, vp, P(vp)],
+        "khy_batch_set_primitive": [vp, vp, st],
+        "khy_batch_set_conserved": [vp, vp, st],
+        "khy_batch_get_conserved": [vp, vp, st],
+        "khy_batch_set_target": [vp, i, d, l],
+        "khy_batch_enqueue_steps": [vp, l],
+        "khy_batch_run": [vp, P(l)],
+        "khy_batch_get_clock": [vp, i, P(d), P(l), P(d)],
+        "khy_batch_autotune": [vp, i, P(i), P(ctypes.c_float)],
+        "khy_batch_set_variant": [vp, i],
+        "khy_batch_profile_steps": [vp, l, P(ctypes.c_float)],
+        "khy_batch_info": [vp, P(ctypes.c_longlong), P(st), P(i), P(i)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -112,6 +128,8 @@ def lib() -> ctypes.CDLL:
         f.restype = ctypes.c_int
     L.khy_destroy.argtypes = [vp]
     L.khy_destroy.restype = None
+    L.khy_batch_destroy.argtypes = [vp]
+    L.khy_batch_destroy.restype = None
     L.khy_last_error.argtypes = []
     L.khy_last_error.restype = ctypes.c_char_p
     L.khy_version.argtypes = []
@@ -297,3 +315,93 @@ class Sim:
 
     def flags(self, clear: bool = False) -> Tuple[int, int]:
         return khy_get_flags(self.h, clear)
+
+
+# ------------------------------------------------------------ many grids
+
+class Batch:
+    """Many independent grids (one ndim, one precision) stepped together."""
+
+    def __init__(self, meshes, stream: Optional[int] = None):
+        self.meshes = list(meshes)
+        arr = (khy_mesh_desc * len(self.meshes))()
+        for k, m in enumerate(self.meshes):
+            arr[k] = desc_of(m)
+        self.h = ctypes.c_void_p()
+        _check(lib().khy_batch_create(arr, len(self.meshes), ctypes.c_void_p(stream or 0), ctypes.byref(self.h)))
+        self.sizes = [m.nvar * m.ncell for m in self.meshes]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+
+    def close(self) -> None:
+        if self.h:
+            lib().khy_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _concat(self, arrays) -> np.ndarray:
+        flat = np.concatenate([np.ascontiguousarray(a, dtype=np.float64).ravel() for a in arrays])
+        assert flat.size == self.offsets[-1]
+        return flat
+
+    def set_primitive(self, Ws) -> None:
+        flat = self._concat(Ws)
+        _check(lib().khy_batch_set_primitive(self.h, ctypes.c_void_p(flat.ctypes.data), flat.size))
+
+    def set_conserved(self, Us) -> None:
+        flat = self._concat(Us)
+        _check(lib().khy_batch_set_conserved(self.h, ctypes.c_void_p(flat.ctypes.data), flat.size))
+
+    def conserved_flat(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(int(self.offsets[-1]), dtype=np.float64)
+        _check(lib().khy_batch_get_conserved(self.h, ctypes.c_void_p(out.ctypes.data), out.size))
+        return out
+
+    def conserved(self):
+        flat = self.conserved_flat()
+        return [flat[self.offsets[k]:self.offsets[k + 1]].reshape(m.shape) for k, m in enumerate(self.meshes)]
+
+    def set_target(self, t_end: float, max_steps: int = -1, grid: int = -1) -> None:
+        _check(lib().khy_batch_set_target(self.h, int(grid), float(t_end), int(max_steps)))
+
+    def enqueue_steps(self, nsteps: int) -> None:
+        _check(lib().khy_batch_enqueue_steps(self.h, int(nsteps)))
+
+    def run(self) -> int:
+        n = ctypes.c_long(0)
+        _check(lib().khy_batch_run(self.h, ctypes.byref(n)))
+        return n.value
+
+    def clock(self, grid: int) -> Tuple[float, int, float]:
+        t, s, dt = ctypes.c_double(), ctypes.c_long(), ctypes.c_double()
+        _check(lib().khy_batch_get_clock(self.h, int(grid), ctypes.byref(t), ctypes.byref(s), ctypes.byref(dt)))
+        return t.value, s.value, dt.value
+
+    def autotune(self, trial_steps: int = 2) -> Tuple[int, float]:
+        v, ms = ctypes.c_int(), ctypes.c_float()
+        _check(lib().khy_batch_autotune(self.h, int(trial_steps), ctypes.byref(v), ctypes.byref(ms)))
+        return v.value, ms.value
+
+    def set_variant(self, v: int) -> None:
+        _check(lib().khy_batch_set_variant(self.h, int(v)))
+
+    def profile_steps(self, nsteps: int) -> Tuple[float, float, float]:
+        ms = (ctypes.c_float * 3)()
+        _check(lib().khy_batch_profile_steps(self.h, int(nsteps), ms))
+        return ms[0], ms[1], ms[2]
+
+    def info(self):
+        cells, pool, v, nb = ctypes.c_longlong(), ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().khy_batch_info(self.h, ctypes.byref(cells), ctypes.byref(pool), ctypes.byref(v), ctypes.byref(nb)))
+        return {"cells": cells.value, "pool_doubles": pool.value, "variant": v.value, "nblocks": nb.value}
