@@ -204,6 +204,54 @@ khy_status khy_batch_profile_steps(khy_batch *b, long nsteps, float ms[3]);
 /* Total cells, pooled doubles per state, current variant, CTAs of the schedule. */
 khy_status khy_batch_info(khy_batch *b, long long *cells, size_t *pool_doubles, int *variant, int *nblocks);
 
+/* ------------------------------------------------------------ serving */
+
+/* A server runs simulation jobs with continuous batching: jobs (2D or 3D
+ * grids, mixed precision, each with its own size, initial state and target
+ * time) are submitted from any thread; a server thread admits each one as
+ * soon as a slot and HBM for its two states are free in the server's arena,
+ * steps all admitted jobs together (one launch per stage per dimensionality,
+ * the batch engine), and retires each job the moment it reaches its target
+ * (result copied to the host, memory and slot freed for the next job).
+ * Every job's result is bitwise equal to the same grid stepped alone. */
+typedef struct khy_server khy_server;
+
+/* Job states reported by khy_server_poll. */
+enum { KHY_JOB_QUEUED = 0, KHY_JOB_ACTIVE = 1, KHY_JOB_DONE = 2, KHY_JOB_FAILED = 3 };
+
+/* Allocates the arena (hbm_budget_bytes of device memory, split in a U half
+ * and a U^1 half), the per-slot clocks (max_slots) and starts the server
+ * thread on the current device.  Errors: KHY_ERR_ARG, KHY_ERR_OOM. */
+khy_status khy_server_create(size_t hbm_budget_bytes, int max_slots, void *cuda_stream, khy_server **out);
+
+/* Stops the server thread (jobs still queued or running are dropped) and
+ * frees everything. */
+void khy_server_destroy(khy_server *s);
+
+/* Queues a job: mesh desc (ndim 2 or 3, KHY_PREC_MIXED), primitive initial
+ * state W (host, count = nvar*ncell doubles, copied), target time t_end > 0.
+ * *job_id receives the job's id.  KHY_ERR_BUDGET if the job's two states
+ * cannot fit the arena even when it is empty. */
+khy_status khy_server_submit(khy_server *s, const khy_mesh_desc *desc, const double *W, size_t count, double t_end,
+                             long *job_id);
+
+/* State (KHY_JOB_*), times in seconds since khy_server_create (submitted,
+ * admitted, finished) and steps taken of a job.  times may be NULL. */
+khy_status khy_server_poll(khy_server *s, long job_id, int *state, double times[3], long *steps);
+
+/* Blocks until the job finished (KHY_OK), failed (KHY_ERR_NONPHYSICAL) or
+ * timeout_s seconds passed (KHY_ERR_TIMEOUT). */
+khy_status khy_server_wait(khy_server *s, long job_id, double timeout_s);
+
+/* Copies a finished job's conserved state to host U (count = nvar*ncell);
+ * release != 0 forgets the job afterwards. */
+khy_status khy_server_result(khy_server *s, long job_id, double *U, size_t count, int release);
+
+/* Completed jobs, active jobs, queued jobs, cell-updates of completed jobs
+ * and seconds since creation. */
+khy_status khy_server_stats(khy_server *s, long *completed, int *active, int *queued,
+                            unsigned long long *cell_updates, double *elapsed_s);
+
 /* ------------------------------------------------------------ no allocation */
 
 /* Capacity, in bytes, of the stage-1 scratch state that khy_step_noalloc

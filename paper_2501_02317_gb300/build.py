@@ -7,6 +7,7 @@ library:
   * khy_runtime.cu -- C ABI, simulation objects, graphs, -fmad=false
   * khy_noalloc.cu -- the allocation-free one-step entry point
   * khy_batch.cu   -- many grids stepped together (batch engine)
+  * khy_server.cu  -- serving loop with continuous batching
 
 ``python -m paper_2501_02317_gb300.build`` builds; ``build()`` is what
 ``__graft_entry__.build()`` calls.
@@ -35,6 +36,7 @@ UNITS = {
     "khy_runtime": ["-fmad=false"],
     "khy_noalloc": ["-fmad=false"],
     "khy_batch": ["-fmad=false"],
+    "khy_server": ["-fmad=false"],
 }
 
 

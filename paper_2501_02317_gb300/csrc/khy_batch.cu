@@ -86,61 +86,15 @@ struct Schedule {
     int nblocks = 0;
 };
 
-// Segment schedule for tile shape (TX, TY): every tile of every grid is a run
-// of planes along its march axis; the runs are cut into CTA shares of equal
-// cost (active cells per plane, plus a fixed per-plane cost, plus the four
-// warm-up planes every run pays).
 Schedule build_schedule(const std::vector<GridDesc> &gd, int ndim, int TX, int TY, int resident) {
-    struct TileRun { int grid, x0, y0, nm; double per_plane; };
-    std::vector<TileRun> runs;
-    double total = 0.0;
-    const double fixed = 0.25 * TX * TY;  // barriers, clock and index work per plane
-    for (int i = 0; i < (int)gd.size(); ++i) {
-        const Geom &g = gd[i].g;
-        const int nm = ndim >= 2 ? g.n[ndim - 1] : 1;
-        const int nty = ndim == 3 ? (g.n[1] + TY - 1) / TY : 1;
-        const int ntx = (g.n[0] + TX - 1) / TX;
-        for (int ty = 0; ty < nty; ++ty)
-            for (int tx = 0; tx < ntx; ++tx) {
-                const int w = std::min(TX, g.n[0] - tx * TX);
-                const int h = ndim == 3 ? std::min(TY, g.n[1] - ty * TY) : 1;
-                TileRun r{i, tx * TX, ty * TY, nm, (double)w * h + fixed};
-                runs.push_back(r);
-                total += r.per_plane * (nm + (ndim >= 2 ? 4 : 0));
-            }
+    std::vector<int> ids(gd.size());
+    std::vector<Geom> geoms(gd.size());
+    for (size_t i = 0; i < gd.size(); ++i) {
+        ids[i] = (int)i;
+        geoms[i] = gd[i].g;
     }
     Schedule s;
-    const int G = std::max(1, std::min(resident, (int)runs.size() * 64));
-    const double quota = total / G;
-    double acc = 0.0;
-    s.cta_seg.push_back(0);
-    const int min_planes = 8;
-    for (const TileRun &r : runs) {
-        int k = 0;
-        while (k < r.nm) {
-            const double warm = ndim >= 2 ? 4.0 * r.per_plane : 0.0;
-            double room = quota - acc - warm;
-            int take = (int)std::floor(room / r.per_plane);
-            const int left = r.nm - k;
-            if (take >= left || left - take < min_planes) take = left;
-            if (take < std::min(min_planes, left)) {
-                if (acc > 0.0 && (int)s.cta_seg.size() - 1 < G - 1) {  // close this CTA, start the next
-                    s.cta_seg.push_back((int)s.segs.size());
-                    acc = 0.0;
-                    continue;
-                }
-                take = std::min(left, std::max(take, std::min(min_planes, left)));
-            }
-            s.segs.push_back(SegDesc{r.grid, r.x0, r.y0, k, k + take});
-            acc += warm + take * r.per_plane;
-            k += take;
-            if (acc >= quota && (int)s.cta_seg.size() - 1 < G - 1) {
-                s.cta_seg.push_back((int)s.segs.size());
-                acc = 0.0;
-            }
-        }
-    }
-    if (s.cta_seg.back() != (int)s.segs.size()) s.cta_seg.push_back((int)s.segs.size());
+    build_segments(ids, geoms, ndim, TX, TY, resident, s.segs, s.cta_seg);
     s.nblocks = (int)s.cta_seg.size() - 1;
     return s;
 }
@@ -288,6 +242,79 @@ khy_status batch_status(const khy_batch *b) {
 }  // namespace
 
 namespace khy {
+// Cost model per plane of a tile run: its active cells plus a fixed part for
+// the barriers and index work; every run (and every piece of a split run)
+// also pays the four warm-up planes of the march.  Boundaries between CTAs
+// are placed at multiples of total/nblocks of the cumulative cost; the total
+// is re-estimated after each pass because splits add warm-up planes.
+void build_segments(const std::vector<int> &ids, const std::vector<Geom> &geoms, int ndim, int TX, int TY,
+                    int nblocks, std::vector<SegDesc> &segs, std::vector<int> &cta_seg) {
+    struct Run { int id, x0, y0, nm; double per; };
+    std::vector<Run> runs;
+    const double fixed = 0.25 * TX * TY;
+    const double warm = ndim >= 2 ? 4.0 : 0.0;
+    double W = 0.0;
+    for (size_t i = 0; i < geoms.size(); ++i) {
+        const Geom &g = geoms[i];
+        const int nm = ndim >= 2 ? g.n[ndim - 1] : 1;
+        const int nty = ndim == 3 ? (g.n[1] + TY - 1) / TY : 1;
+        const int ntx = (g.n[0] + TX - 1) / TX;
+        for (int b = 0; b < nty; ++b)
+            for (int a = 0; a < ntx; ++a) {
+                const int w = std::min(TX, g.n[0] - a * TX);
+                const int h = ndim == 3 ? std::min(TY, g.n[1] - b * TY) : 1;
+                runs.push_back(Run{ids[i], a * TX, b * TY, nm, (double)w * h + fixed});
+                W += runs.back().per * (nm + warm);
+            }
+    }
+    const int min_planes = 8;
+    const int G = std::max(1, std::min<int>(nblocks, (int)std::min<size_t>(runs.size() * 64, 1 << 30)));
+    for (int pass = 0; pass < 3; ++pass) {
+        segs.clear();
+        cta_seg.assign(1, 0);
+        int cta = 0;
+        double C = 0.0, bound = W / G;
+        auto close_cta = [&]() {
+            if (cta < G - 1) {
+                cta_seg.push_back((int)segs.size());
+                ++cta;
+                bound = (cta + 1) * W / G;
+            }
+        };
+        for (const Run &r : runs) {
+            int k = 0;
+            while (k < r.nm) {
+                const double full = (warm + (r.nm - k)) * r.per;
+                if (C + full <= bound || cta == G - 1 || ndim == 1) {
+                    segs.push_back(SegDesc{r.id, r.x0, r.y0, k, r.nm});
+                    C += full;
+                    k = r.nm;
+                    if (C >= bound) close_cta();
+                    continue;
+                }
+                int take = (int)std::floor((bound - C) / r.per - warm);
+                if (take < min_planes) {
+                    if ((int)segs.size() > cta_seg.back()) {  // this CTA has work: start the next one
+                        close_cta();
+                        continue;
+                    }
+                    take = min_planes;
+                }
+                if (r.nm - k - take < min_planes) take = r.nm - k;
+                segs.push_back(SegDesc{r.id, r.x0, r.y0, k, k + take});
+                C += (warm + take) * r.per;
+                k += take;
+                close_cta();
+            }
+        }
+        if (cta_seg.back() != (int)segs.size()) cta_seg.push_back((int)segs.size());
+        if (C <= W * 1.0001) break;
+        W = C;  // splits added warm-up planes: re-cut with the real total
+    }
+    // drop empty CTAs at the end
+    while (cta_seg.size() > 2 && cta_seg[cta_seg.size() - 2] == cta_seg.back()) cta_seg.pop_back();
+}
+
 void multi_variant_tile(int ndim, int variant, int *tx, int *ty) {
     static const int table[4][kMultiVariants][2] = {
         {{0, 0}, {0, 0}, {0, 0}}, {{128, 1}, {256, 1}, {0, 0}}, {{64, 1}, {128, 1}, {256, 1}}, {{32, 8}, {32, 16}, {0, 0}}};

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "khy_stage.cuh"
 
 namespace khy {
@@ -32,6 +34,12 @@ cudaError_t launch_multi_dt_fp64(const MultiArgs &a, int ndim, int variant, int 
 cudaError_t launch_multi_dt_mixed(const MultiArgs &a, int ndim, int variant, int nblocks, cudaStream_t s);
 int multi_resident_fp64(int ndim, int variant);
 int multi_resident_mixed(int ndim, int variant);
+
+// Segment schedule for many grids (khy_batch.cu): every tile of every grid
+// (ids[i] names grid i in the SegDesc) is a run of planes along its march
+// axis; the runs are cut at nblocks equal shares of the estimated cost.
+void build_segments(const std::vector<int> &ids, const std::vector<Geom> &geoms, int ndim, int TX, int TY,
+                    int nblocks, std::vector<SegDesc> &segs, std::vector<int> &cta_seg);
 
 // Sets the shared-memory limits of the stage kernels of one dimensionality
 // and caches their persistent grid sizes; call before the first launch (in

@@ -83,12 +83,16 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
     const long long N = g.ncell;
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
+    // active extent of this tile (ragged tiles and grids narrower than a tile)
+    const int wact = min(TX, g.n[0] - x0);
+    const int hact = (ND == 3) ? min(TY, g.n[1] - y0) : 1;
 
     // plane L of the march axis (ignored in 1D) -> ring slot
     auto load_plane = [&](int L, int slot) {
         R *dst = sW + (size_t)slot * NV * PC;
         for (int e = tid; e < PC; e += NT) {
             const int hx = e % PX, hy = e / PX;
+            if (hx >= wact + 4 || (ND == 3 && hy >= hact + 4)) continue;  // outside the active halo box
             int act[3] = {0, 0, 0};
             int c[3] = {0, 0, 0};
             c[0] = bc_map(x0 - 2 + hx, g.n[0], g.bc[0][0], g.bc[0][1], &act[0]);
@@ -139,6 +143,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
             R s[4][NV], F[NV];
             if (f < T::NXF) {
                 const int fx = f % (TX + 1), fy = f / (TX + 1);
+                if (fx > wact || fy >= hact) continue;
                 const int hy = (ND == 3) ? fy + 2 : 0;
                 gather(pl, hy * PX + fx, 1, s);
                 face_flux<ND, R>(s, 0, kc, F);
@@ -147,6 +152,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
             } else {
                 const int f2 = f - T::NXF;
                 const int fxx = f2 % TX, fyy = f2 / TX;
+                if (fxx >= wact || fyy > hact) continue;
                 gather(pl, fyy * PX + fxx + 2, PX, s);
                 face_flux<ND, R>(s, 1, kc, F);
 #pragma unroll
@@ -238,7 +244,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
             __syncthreads();
             if (L >= k0 + 1) {
                 const int cur = L - 2;
-                {   // march-axis face between cur and cur+1, from planes cur-1 .. cur+2
+                if (tx < wact && ty < hact) {  // march-axis face between cur and cur+1, planes cur-1 .. cur+2
                     R s[4][NV];
                     const int e = (ND == 3) ? (ty + 2) * PX + tx + 2 : tx + 2;
 #pragma unroll

@@ -36,7 +36,8 @@ EXPORTS = [
     "khy_batch_create", "khy_batch_destroy", "khy_batch_set_primitive", "khy_batch_set_conserved",
     "khy_batch_get_conserved", "khy_batch_set_target", "khy_batch_enqueue_steps", "khy_batch_run",
     "khy_batch_get_clock", "khy_batch_autotune", "khy_batch_set_variant", "khy_batch_profile_steps",
-    "khy_batch_info",
+    "khy_batch_info", "khy_server_create", "khy_server_destroy", "khy_server_submit", "khy_server_poll",
+    "khy_server_wait", "khy_server_result", "khy_server_stats",
 ]
 
 
@@ -121,6 +122,12 @@ def lib() -> ctypes.CDLL:
         "khy_batch_set_variant": [vp, i],
         "khy_batch_profile_steps": [vp, l, P(ctypes.c_float)],
         "khy_batch_info": [vp, P(ctypes.c_longlong), P(st), P(i), P(i)],
+        "khy_server_create": [st, i, vp, P(vp)],
+        "khy_server_submit": [vp, P(khy_mesh_desc), vp, st, d, P(l)],
+        "khy_server_poll": [vp, l, P(i), P(d), P(l)],
+        "khy_server_wait": [vp, l, d],
+        "khy_server_result": [vp, l, vp, st, i],
+        "khy_server_stats": [vp, P(l), P(i), P(i), P(ctypes.c_ulonglong), P(d)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -130,6 +137,8 @@ def lib() -> ctypes.CDLL:
     L.khy_destroy.restype = None
     L.khy_batch_destroy.argtypes = [vp]
     L.khy_batch_destroy.restype = None
+    L.khy_server_destroy.argtypes = [vp]
+    L.khy_server_destroy.restype = None
     L.khy_last_error.argtypes = []
     L.khy_last_error.restype = ctypes.c_char_p
     L.khy_version.argtypes = []
@@ -405,3 +414,68 @@ class Batch:
         cells, pool, v, nb = ctypes.c_longlong(), ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
         _check(lib().khy_batch_info(self.h, ctypes.byref(cells), ctypes.byref(pool), ctypes.byref(v), ctypes.byref(nb)))
         return {"cells": cells.value, "pool_doubles": pool.value, "variant": v.value, "nblocks": nb.value}
+
+
+# ------------------------------------------------------------ serving
+
+JOB_QUEUED, JOB_ACTIVE, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
+
+
+class Server:
+    """Continuous-batching job server (a thread of libkhydro.so)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 256, stream: Optional[int] = None):
+        self.h = ctypes.c_void_p()
+        _check(lib().khy_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.c_void_p(stream or 0),
+                                       ctypes.byref(self.h)))
+        self.meshes = {}
+
+    def close(self) -> None:
+        if self.h:
+            lib().khy_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, mesh: Mesh, W: np.ndarray, t_end: float) -> int:
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        desc = desc_of(mesh)
+        jid = ctypes.c_long()
+        _check(lib().khy_server_submit(self.h, ctypes.byref(desc), ctypes.c_void_p(W.ctypes.data), W.size,
+                                       float(t_end), ctypes.byref(jid)))
+        self.meshes[jid.value] = mesh
+        return jid.value
+
+    def poll(self, job: int):
+        st, steps = ctypes.c_int(), ctypes.c_long()
+        times = (ctypes.c_double * 3)()
+        _check(lib().khy_server_poll(self.h, int(job), ctypes.byref(st), times, ctypes.byref(steps)))
+        return st.value, (times[0], times[1], times[2]), steps.value
+
+    def wait(self, job: int, timeout_s: float = 600.0) -> None:
+        _check(lib().khy_server_wait(self.h, int(job), float(timeout_s)))
+
+    def result(self, job: int, release: bool = False) -> np.ndarray:
+        mesh = self.meshes[job]
+        out = np.empty(mesh.shape, dtype=np.float64)
+        _check(lib().khy_server_result(self.h, int(job), ctypes.c_void_p(out.ctypes.data), out.size, int(release)))
+        if release:
+            self.meshes.pop(job, None)
+        return out
+
+    def stats(self):
+        c, a, q, cu, el = ctypes.c_long(), ctypes.c_int(), ctypes.c_int(), ctypes.c_ulonglong(), ctypes.c_double()
+        _check(lib().khy_server_stats(self.h, ctypes.byref(c), ctypes.byref(a), ctypes.byref(q), ctypes.byref(cu),
+                                      ctypes.byref(el)))
+        return {"completed": c.value, "active": a.value, "queued": q.value, "cell_updates": cu.value,
+                "elapsed_s": el.value}
