@@ -139,6 +139,78 @@ def cpu_oracle_rate(seconds: float = 10.0, n: int = 128):
     return mesh.ncell * steps / el, used, "%d Heun steps of the %d^3 turbulence box (same recipe, seed 2)" % (steps, n)
 
 
+def bench_batch(khydro, wl, torch, steps: int = 200):
+    """Batched workload: 4096 independent 2D blast grids (sides log-uniform in
+    [32, 256], seed 3), mixed precision, one launch per stage for all grids,
+    tile variant picked by the autotuner; `steps` Heun steps of every grid."""
+    grids = wl.batch_blasts(4096)
+    meshes = [m for m, _ in grids]
+    cells = sum(m.ncell for m in meshes)
+    stream = torch.cuda.Stream()
+    with khydro.Batch(meshes, stream=stream.cuda_stream) as b:
+        b.set_primitive([W for _, W in grids])
+        variant, tune_ms = b.autotune(2)
+        b.set_target(1e30, steps)
+        b.enqueue_steps(3)
+        torch.cuda.synchronize()
+        b.set_target(1e30, steps)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.enqueue_steps(steps)
+        e1.record(stream)
+        e1.synchronize()
+        el = e0.elapsed_time(e1) / 1e3
+        info = b.info()
+        done = all(b.clock(k)[1] == steps + 3 for k in (0, len(meshes) // 2, len(meshes) - 1))
+    return {"workload": "4096 2D blast grids, sides log-U[32,256] (seed 3), mixed, periodic", "grids": len(meshes),
+            "cells": cells, "steps": steps, "value": cells * steps / el, "unit": UNIT, "ms_per_step": 1e3 * el / steps,
+            "variant": variant, "ctas": info["nblocks"], "launches_per_step": 3, "all_grids_stepped": done}
+
+
+def bench_serving(khydro, wl, njobs: int = 60, budget_bytes: int = 16 << 30, slots: int = 64):
+    """Serving: the first `njobs` jobs of the seeded Poisson stream (200/s;
+    2D 64^2-512^2 and 3D 32^3-128^3, KH / blast / turbulence, t_end U[0.05, 0.5])
+    submitted at their arrival times; then the same jobs at 50% and 90% of the
+    measured capacity.  Time-to-solution = finish - submit."""
+    jobs = wl.serving_stream(njobs, seed=4)
+    ics = [wl.job_initial_state(j) for j in jobs]
+
+    def run(arrivals):
+        with khydro.Server(budget_bytes, slots) as srv:
+            t0 = time.perf_counter()
+            ids = []
+            for (m, W), j, at in zip(ics, jobs, arrivals):
+                delay = at - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                ids.append(srv.submit(m, W, j.t_end))
+            for i in ids:
+                srv.wait(i, 1800.0)
+            lat = []
+            for i in ids:
+                _, (ts, ta, td), _ = srv.poll(i)
+                lat.append(td - ts)
+            st = srv.stats()
+        makespan = st["elapsed_s"]
+        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "value": st["cell_updates"] / makespan, "jobs": len(ids), "makespan_s": makespan,
+                "cell_updates": st["cell_updates"]}
+
+    base = [j.arrival for j in jobs]
+    sat = run(base)
+    cap = njobs / sat["makespan_s"]  # jobs/s the server sustained while saturated
+    out = {"workload": "Poisson 200 jobs/s (seed 4), first %d jobs, mixed, HBM budget %d GiB, %d slots"
+                       % (njobs, budget_bytes >> 30, slots),
+           "offered_200_per_s": sat, "capacity_jobs_per_s": cap}
+    for frac in (0.5, 0.9):
+        rate = frac * cap
+        arr = [k / rate for k in range(njobs)]
+        out["load_%d%%" % int(frac * 100)] = run(arr)
+    out["unit"] = UNIT
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -163,7 +235,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "turbulence-3d-%d^3-fp64-oracle" % n, "cells": mesh.ncell},
+        "config": {"workload": "turbulence-3d-%d^3-mixed" % args.n, "cells": (args.n ** 3),
+                   "sample": "oracle (FP64) on a %d^3 box of the same recipe, %d cells" % (n, mesh.ncell)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -180,6 +253,8 @@ def main():
     ap.add_argument("--n", type=int, default=256, help="side of the 3D turbulence box")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-grids measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -277,6 +352,9 @@ def main():
                "api": "khy_set_conserved(host) + khy_enqueue_steps(1) + khy_get_conserved(host)"}
     sim.close()
 
+    batch = None if args.no_batch or world > 1 else bench_batch(khydro, wl, torch)
+    serving = None if args.no_serve or world > 1 else bench_serving(khydro, wl)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, cores, sample = cpu_oracle_rate()
@@ -301,6 +379,8 @@ def main():
                          "bytes_per_cell_update": BYTES_PER_CELL_UPDATE_3D, "stage_ms": [ms[1], ms[2]],
                          "clock_ms": ms[0], "peak_kind": peak_kind},
             "cpu_baseline": cpu,
+            "batch": batch,
+            "serving": serving,
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": 3 * K,
