@@ -183,12 +183,16 @@ __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a,
 __device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
-__device__ __forceinline__ double rsqrt_(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ double rroot(double a) { return __dsqrt_rn(a); }
+// FP32 (mixed path): division and square root use the special-function
+// unit's approximations (a few ulp, far inside the mixed path's tolerance);
+// they are still pure functions of their inputs, so redundant face fluxes
+// stay bitwise identical.
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
-__device__ __forceinline__ float rsqrt_(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float rroot(float a) { return a > 0.f ? __fmul_rn(a, rsqrtf(a)) : 0.f; }
 
 // ------------------------------------------------------------ Sec. 3.2.2
 // HLLC flux for rotated primitive states w = (rho, u, t_1..t_NT, p), NT
@@ -200,24 +204,24 @@ __device__ __forceinline__ void hllc(const Consts<R> &k, const R (&wl)[NT + 3], 
     constexpr int P = NT + 2;  // pressure slot
     const R rl = wl[0], ul = wl[1], pl = wl[P];
     const R rr = wr[0], ur = wr[1], pr = wr[P];
-    const R cl = rsqrt_(rdiv(rmul(k.gamma, pl), rl));
-    const R cr = rsqrt_(rdiv(rmul(k.gamma, pr), rr));
+    const R cl = rroot(rdiv(rmul(k.gamma, pl), rl));
+    const R cr = rroot(rdiv(rmul(k.gamma, pr), rr));
     // p* estimate: PVRS clamped at 0; the two-shock estimate when both waves are shocks
     const R ppv = rsub(rmul(R(0.5), radd(pl, pr)),
                        rmul(rmul(rmul(R(0.125), rsub(ur, ul)), radd(rl, rr)), radd(cl, cr)));
     R pstar = ppv > R(0) ? ppv : R(0);
     const R pmax = pl > pr ? pl : pr;
     if (pstar > pmax) {
-        const R gl = rsqrt_(rdiv(rdiv(R(2), rmul(k.gp1, rl)), radd(pstar, rmul(k.gm1_gp1, pl))));
-        const R gr = rsqrt_(rdiv(rdiv(R(2), rmul(k.gp1, rr)), radd(pstar, rmul(k.gm1_gp1, pr))));
+        const R gl = rroot(rdiv(rdiv(R(2), rmul(k.gp1, rl)), radd(pstar, rmul(k.gm1_gp1, pl))));
+        const R gr = rroot(rdiv(rdiv(R(2), rmul(k.gp1, rr)), radd(pstar, rmul(k.gm1_gp1, pr))));
         pstar = rdiv(rsub(radd(rmul(gl, pl), rmul(gr, pr)), rsub(ur, ul)), radd(gl, gr));
     }
     R ratl = rdiv(pstar, pl), ratr = rdiv(pstar, pr);
     if (ratl < R(1)) ratl = R(1);
     if (ratr < R(1)) ratr = R(1);
     // Eq. 5: q_K and the subtraction-safe offsets ds_K = s_K - u_K
-    const R ql = rsqrt_(radd(R(1), rmul(k.g1, rsub(ratl, R(1)))));
-    const R qr = rsqrt_(radd(R(1), rmul(k.g1, rsub(ratr, R(1)))));
+    const R ql = rroot(radd(R(1), rmul(k.g1, rsub(ratl, R(1)))));
+    const R qr = rroot(radd(R(1), rmul(k.g1, rsub(ratr, R(1)))));
     const R dsl = rmul(-cl, ql);
     const R dsr = rmul(cr, qr);
     const R sl = radd(ul, dsl);

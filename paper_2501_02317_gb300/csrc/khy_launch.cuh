@@ -119,7 +119,7 @@ struct VariantTile { int tx, ty; };
 __host__ __device__ constexpr VariantTile variant_tile(int ndim, int v) {
     return ndim == 1 ? (v == 0 ? VariantTile{128, 1} : v == 1 ? VariantTile{256, 1} : VariantTile{0, 0})
          : ndim == 2 ? (v == 0 ? VariantTile{64, 1} : v == 1 ? VariantTile{128, 1} : v == 2 ? VariantTile{256, 1} : VariantTile{0, 0})
-         : ndim == 3 ? (v == 0 ? VariantTile{32, 8} : v == 1 ? VariantTile{32, 16} : VariantTile{0, 0})
+         : ndim == 3 ? (v == 0 ? VariantTile{32, 8} : v == 1 ? VariantTile{32, 16} : v == 2 ? VariantTile{64, 8} : VariantTile{0, 0})
                      : VariantTile{0, 0};
 }
 
@@ -148,6 +148,7 @@ static cudaError_t launch_multi_stage_prec(const MultiArgs &a, int ndim, int v, 
         case 22: return multi_stage_v<R, 2, 2>(a, stage, nblocks, s);
         case 30: return multi_stage_v<R, 3, 0>(a, stage, nblocks, s);
         case 31: return multi_stage_v<R, 3, 1>(a, stage, nblocks, s);
+        case 32: return multi_stage_v<R, 3, 2>(a, stage, nblocks, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -171,6 +172,7 @@ static int multi_resident_prec(int ndim, int v) {
         case 22: return multi_resident_v<R, 2, 2>();
         case 30: return multi_resident_v<R, 3, 0>();
         case 31: return multi_resident_v<R, 3, 1>();
+        case 32: return multi_resident_v<R, 3, 2>();
         default: return 0;
     }
 }

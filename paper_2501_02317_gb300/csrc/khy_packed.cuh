@@ -1,0 +1,140 @@
+// khy_packed.cuh -- two face fluxes per thread with Blackwell's packed FP32
+// instructions (mixed path).
+//
+// The FP32 part of the mixed stage (PLM + HLLC, Sec. 3.2.2) is most of its
+// instructions.  sm_100+ executes FADD2 / FMUL2 / FFMA2: one instruction for
+// two independent FP32 operations.  Every face of the mixed path is computed
+// by face_flux2 below, two faces per call (the x and y lanes of float2
+// values); lanes never mix, so a face has the same bits whichever thread,
+// lane or CTA computes it.  Divisions and square roots are per lane on the
+// special-function unit; comparisons and branch choices are per-lane selects.
+#pragma once
+
+#include "khy_kernels.cuh"
+
+namespace khy {
+namespace pk {
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b == a + b * (-1), rounded once: identical to a rounded subtraction
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 div2(float2 a, float2 b) { return make_float2(rdiv(a.x, b.x), rdiv(a.y, b.y)); }
+__device__ __forceinline__ float2 root2(float2 a) { return make_float2(rroot(a.x), rroot(a.y)); }
+__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
+    return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
+}
+__device__ __forceinline__ float2 max2(float2 a, float2 b) { return make_float2(a.x > b.x ? a.x : b.x, a.y > b.y ? a.y : b.y); }
+
+__device__ __forceinline__ float minmod1(float a, float b) {
+    const bool same = (a > 0.f && b > 0.f) || (a < 0.f && b < 0.f);
+    if (!same) return 0.f;
+    return fabsf(a) < fabsf(b) ? a : b;
+}
+__device__ __forceinline__ float2 minmod2(float2 a, float2 b) { return make_float2(minmod1(a.x, b.x), minmod1(a.y, b.y)); }
+
+// HLLC flux of two faces (lanes), rotated primitives (rho, u, t_1..t_NT, p):
+// the same estimate of p* (PVRS, two-shock above both pressures), the same
+// Eq. 4 / Eq. 5 speeds and the same branch order as the scalar hllc().
+template <int NT>
+__device__ __forceinline__ void hllc2(const Consts<float> &k, const float2 (&wl)[NT + 3], const float2 (&wr)[NT + 3],
+                                      float2 (&F)[NT + 3]) {
+    constexpr int P = NT + 2;
+    const float2 rl = wl[0], ul = wl[1], pl = wl[P];
+    const float2 rr = wr[0], ur = wr[1], pr = wr[P];
+    const float2 g = splat(k.gamma);
+    const float2 cl = root2(div2(mul2(g, pl), rl));
+    const float2 cr = root2(div2(mul2(g, pr), rr));
+    const float2 du = sub2(ur, ul);
+    const float2 ppv = sub2(mul2(splat(0.5f), add2(pl, pr)), mul2(mul2(mul2(splat(0.125f), du), add2(rl, rr)), add2(cl, cr)));
+    float2 pstar = max2(ppv, splat(0.f));
+    const float2 pmax = max2(pl, pr);
+    const bool tx = pstar.x > pmax.x, ty = pstar.y > pmax.y;
+    if (tx || ty) {  // both waves shocks in at least one lane: two-shock estimate
+        const float2 two = splat(2.f), gp1 = splat(k.gp1), gg = splat(k.gm1_gp1);
+        const float2 gl = root2(div2(div2(two, mul2(gp1, rl)), fma2(gg, pl, pstar)));
+        const float2 gr = root2(div2(div2(two, mul2(gp1, rr)), fma2(gg, pr, pstar)));
+        const float2 pts = div2(sub2(fma2(gl, pl, mul2(gr, pr)), du), add2(gl, gr));
+        pstar = sel2(tx, ty, pts, pstar);
+    }
+    const float2 one = splat(1.f);
+    const float2 ratl = max2(div2(pstar, pl), one);
+    const float2 ratr = max2(div2(pstar, pr), one);
+    const float2 ql = root2(fma2(splat(k.g1), sub2(ratl, one), one));
+    const float2 qr = root2(fma2(splat(k.g1), sub2(ratr, one), one));
+    const float2 dsl = mul2(splat(-1.f), mul2(cl, ql));
+    const float2 dsr = mul2(cr, qr);
+    const float2 sl = add2(ul, dsl);
+    const float2 sr = add2(ur, dsr);
+    const float2 sstar = div2(sub2(sub2(pr, mul2(mul2(rr, ur), dsr)), sub2(pl, mul2(mul2(rl, ul), dsl))),
+                              sub2(mul2(rl, dsl), mul2(rr, dsr)));
+    // branch order: 0 <= s_L -> F_L; 0 <= s* -> F*_L; 0 < s_R -> F*_R; else F_R
+    const bool lx = (0.f <= sl.x) || (0.f <= sstar.x), ly = (0.f <= sl.y) || (0.f <= sstar.y);
+    const bool ox = lx ? (0.f <= sl.x) : !(0.f < sr.x), oy = ly ? (0.f <= sl.y) : !(0.f < sr.y);
+    float2 w[NT + 3];
+#pragma unroll
+    for (int j = 0; j < NT + 3; ++j) w[j] = sel2(lx, ly, wl[j], wr[j]);
+    const float2 rk = w[0], uk = w[1], pk = w[P];
+    const float2 sk = sel2(lx, ly, sl, sr);
+    const float2 dsk = sel2(lx, ly, dsl, dsr);
+    float2 vsq = mul2(uk, uk);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) vsq = fma2(w[2 + j], w[2 + j], vsq);
+    const float2 E = fma2(mul2(splat(0.5f), rk), vsq, div2(pk, splat(k.gm1)));
+    const float2 mf = mul2(rk, uk);
+    float2 Uk[NT + 3], Fk[NT + 3];
+    Uk[0] = rk;
+    Uk[1] = mf;
+    Fk[0] = mf;
+    Fk[1] = fma2(mf, uk, pk);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        Uk[2 + j] = mul2(rk, w[2 + j]);
+        Fk[2 + j] = mul2(mf, w[2 + j]);
+    }
+    Uk[P] = E;
+    Fk[P] = mul2(add2(E, pk), uk);
+    const float2 fac = div2(mul2(rk, dsk), sub2(sk, sstar));
+    float2 Us[NT + 3];
+    Us[0] = fac;
+    Us[1] = mul2(fac, sstar);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) Us[2 + j] = mul2(fac, w[2 + j]);
+    Us[P] = mul2(fac, fma2(sub2(sstar, uk), add2(sstar, div2(pk, mul2(rk, dsk))), div2(Uk[P], rk)));
+#pragma unroll
+    for (int q = 0; q < NT + 3; ++q) F[q] = sel2(ox, oy, Fk[q], fma2(sk, sub2(Us[q], Uk[q]), Fk[q]));
+}
+
+// Storage slot of rotated component j (0 rho, 1 normal velocity, 2..ND
+// transverse velocities in increasing axis order, ND+1 pressure) for a face
+// normal to direction dir.
+template <int ND>
+__device__ __forceinline__ int rot_slot(int dir, int j) {
+    if (j == 0) return 0;
+    if (j == ND + 1) return ND + 1;
+    if (j == 1) return 1 + dir;
+    if (j == 2) return 1 + (dir == 0 ? 1 : 0);
+    return 1 + (dir == 2 ? 1 : 2);
+}
+
+// Two face fluxes (lanes) from two four-cell stencils already rotated onto
+// their face normals: packed minmod PLM, then packed HLLC.  Fr is in rotated
+// order (mass, normal momentum, transverse momenta, energy).
+template <int ND>
+__device__ __forceinline__ void face_flux2(const float2 (&st)[4][ND + 2], const Consts<float> &k, float2 (&Fr)[ND + 2]) {
+    constexpr int NT = ND - 1;
+    float2 wl[NT + 3], wr[NT + 3];
+    const float2 half = splat(0.5f), mhalf = splat(-0.5f);
+#pragma unroll
+    for (int j = 0; j < ND + 2; ++j) {
+        const float2 d12 = sub2(st[2][j], st[1][j]);
+        wl[j] = fma2(minmod2(sub2(st[1][j], st[0][j]), d12), half, st[1][j]);
+        wr[j] = fma2(minmod2(d12, sub2(st[3][j], st[2][j])), mhalf, st[2][j]);
+    }
+    hllc2<NT>(k, wl, wr, Fr);
+}
+
+}  // namespace pk
+}  // namespace khy

@@ -37,6 +37,7 @@
 
 #include "khy_kernels.cuh"
 #include "khy_mixed_kernels.cuh"
+#include "khy_packed.cuh"
 
 namespace khy {
 
@@ -59,9 +60,12 @@ struct Tile {
     static constexpr int NT = TX * TY;
     static constexpr int NXF = (TX + 1) * TY;
     static constexpr int NYF = (ND == 3) ? TX * (TY + 1) : 0;
+    // mixed path: march-axis fluxes of the last two planes also live in shared memory
+    static constexpr int NFM = (ND >= 2) ? 2 * NV * NT : 0;
     template <class R>
     static constexpr size_t smem_bytes() {
-        return sizeof(R) * ((size_t)NSLOT * NV * PC + (size_t)NV * NXF + (size_t)NV * NYF);
+        return sizeof(R) * ((size_t)NSLOT * NV * PC + (size_t)NV * NXF + (size_t)NV * NYF +
+                            (std::is_same<R, float>::value ? (size_t)NFM : 0));
     }
 };
 
@@ -79,6 +83,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
     constexpr int NV = T::NV, PX = T::PX, PC = T::PC, NT = T::NT;
     constexpr int DM = ND - 1;  // march axis (ND >= 2)
     const Consts<R> kc = make_consts<R>(g);
+    const Consts<float> kc_f = make_consts<float>(g);
     const mx::MixConsts mk = mx::make_mix(g);
     const long long N = g.ncell;
     const int tid = threadIdx.x;
@@ -87,20 +92,30 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
     const int wact = min(TX, g.n[0] - x0);
     const int hact = (ND == 3) ? min(TY, g.n[1] - y0) : 1;
 
+    // tiles whose halo box lies inside the grid skip the ghost-zone index map
+    const bool x_inside = x0 >= 2 && x0 + wact + 2 <= g.n[0];
+    const bool y_inside = ND != 3 || (y0 >= 2 && y0 + hact + 2 <= g.n[1]);
+
     // plane L of the march axis (ignored in 1D) -> ring slot
     auto load_plane = [&](int L, int slot) {
         R *dst = sW + (size_t)slot * NV * PC;
+        int actm = 0;  // the march-axis index map is the same for the whole plane
+        const int cm = (ND >= 2) ? bc_map(L, g.n[DM], g.bc[DM][0], g.bc[DM][1], &actm) : 0;
         for (int e = tid; e < PC; e += NT) {
             const int hx = e % PX, hy = e / PX;
             if (hx >= wact + 4 || (ND == 3 && hy >= hact + 4)) continue;  // outside the active halo box
             int act[3] = {0, 0, 0};
             int c[3] = {0, 0, 0};
-            c[0] = bc_map(x0 - 2 + hx, g.n[0], g.bc[0][0], g.bc[0][1], &act[0]);
+            if (x_inside) c[0] = x0 - 2 + hx;
+            else c[0] = bc_map(x0 - 2 + hx, g.n[0], g.bc[0][0], g.bc[0][1], &act[0]);
             if (ND == 3) {
-                c[1] = bc_map(y0 - 2 + hy, g.n[1], g.bc[1][0], g.bc[1][1], &act[1]);
-                c[2] = bc_map(L, g.n[2], g.bc[2][0], g.bc[2][1], &act[2]);
+                if (y_inside) c[1] = y0 - 2 + hy;
+                else c[1] = bc_map(y0 - 2 + hy, g.n[1], g.bc[1][0], g.bc[1][1], &act[1]);
+                c[2] = cm;
+                act[2] = actm;
             } else if (ND == 2) {
-                c[1] = bc_map(L, g.n[1], g.bc[1][0], g.bc[1][1], &act[1]);
+                c[1] = cm;
+                act[1] = actm;
             }
             const long long idx = ((long long)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
             double u[NV];
@@ -157,6 +172,87 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
                 face_flux<ND, R>(s, 1, kc, F);
 #pragma unroll
                 for (int q = 0; q < NV; ++q) sFy[(size_t)q * T::NYF + f2] = F[q];
+            }
+        }
+    };
+
+    // mixed path: every face of a plane (march-axis faces of all columns, then
+    // the in-plane faces) as a list of tasks, two per packed face_flux2 call;
+    // march fluxes go to sFm[cur & 1], in-plane ones to sFx / sFy.
+    R *sFm = sFy + (size_t)NV * T::NYF;  // [2][NV][NT], mixed path only
+    auto faces_mix = [&](int cur, bool inplane) {
+        constexpr int NTM = (ND >= 2) ? NT : 0;
+        const int ntask = NTM + (inplane ? T::NXF + T::NYF : 0);
+        const float *cp = reinterpret_cast<const float *>(sW);
+        // task tau -> plane offsets of its four stencil cells (slot base o*step
+        // plus e0 + o*stride), face direction, destination; false if inactive
+        struct Task {
+            int pbase, pstep, e0, stride, dir, dstride;
+            float *dst;
+        };
+        auto decode = [&](int tau, Task &t) -> bool {
+            if (tau < NTM) {
+                const int ctx = tau % TX, cty = tau / TX;
+                if (ctx >= wact || cty >= hact) return false;
+                t.e0 = (ND == 3) ? (cty + 2) * PX + ctx + 2 : ctx + 2;
+                t.stride = 0;
+                t.pbase = cur - 1;  // planes cur-1 .. cur+2
+                t.pstep = 1;
+                t.dir = DM;
+                t.dst = reinterpret_cast<float *>(sFm) + (size_t)(cur & 1) * NV * NT + tau;
+                t.dstride = NT;
+                return true;
+            }
+            const int f = tau - NTM;
+            t.pbase = cur;
+            t.pstep = 0;
+            if (f < T::NXF) {
+                const int fx = f % (TX + 1), fy = f / (TX + 1);
+                if (fx > wact || fy >= hact) return false;
+                t.e0 = ((ND == 3) ? fy + 2 : 0) * PX + fx;
+                t.stride = 1;
+                t.dir = 0;
+                t.dst = reinterpret_cast<float *>(sFx) + f;
+                t.dstride = T::NXF;
+            } else {
+                const int f2 = f - T::NXF;
+                const int fxx = f2 % TX, fyy = f2 / TX;
+                if (fxx >= wact || fyy > hact) return false;
+                t.e0 = fyy * PX + fxx + 2;
+                t.stride = PX;
+                t.dir = 1;
+                t.dst = reinterpret_cast<float *>(sFy) + f2;
+                t.dstride = T::NYF;
+            }
+            return true;
+        };
+        for (int pr = tid; 2 * pr < ntask; pr += NT) {
+            Task ta, tb;
+            const bool va = decode(2 * pr, ta);
+            const bool vb = (2 * pr + 1 < ntask) && decode(2 * pr + 1, tb);
+            if (!va && !vb) continue;
+            if (!va) ta = tb;  // an idle lane recomputes its partner's face and stores nothing
+            if (!vb) tb = ta;
+            // gather both stencils already rotated onto their face normals
+            float2 st[4][NV];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const float *pa = cp + (size_t)((ta.pbase + o * ta.pstep) & 3) * NV * PC + ta.e0 + o * ta.stride;
+                const float *pb = cp + (size_t)((tb.pbase + o * tb.pstep) & 3) * NV * PC + tb.e0 + o * tb.stride;
+#pragma unroll
+                for (int j = 0; j < NV; ++j)
+                    st[o][j] = make_float2(pa[(size_t)pk::rot_slot<ND>(ta.dir, j) * PC],
+                                           pb[(size_t)pk::rot_slot<ND>(tb.dir, j) * PC]);
+            }
+            float2 Fr[NV];
+            pk::face_flux2<ND>(st, kc_f, Fr);
+            if (va) {
+#pragma unroll
+                for (int j = 0; j < NV; ++j) ta.dst[(size_t)pk::rot_slot<ND>(ta.dir, j) * ta.dstride] = Fr[j].x;
+            }
+            if (vb) {
+#pragma unroll
+                for (int j = 0; j < NV; ++j) tb.dst[(size_t)pk::rot_slot<ND>(tb.dir, j) * tb.dstride] = Fr[j].y;
             }
         }
     };
@@ -230,11 +326,33 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
     if (ND == 1) {
         load_plane(0, 0);
         __syncthreads();
-        inplane_faces(0);
+        if constexpr (MIX) faces_mix(0, true);
+        else inplane_faces(0);
         __syncthreads();
         R dummy[NV];
         update_cell(0, dummy, dummy);
         __syncthreads();
+    } else if constexpr (MIX) {
+        for (int L = k0 - 2; L <= k1 + 1; ++L) {
+            load_plane(L, L & 3);
+            __syncthreads();
+            if (L >= k0 + 1) {
+                const int cur = L - 2;
+                faces_mix(cur, cur >= k0);
+                __syncthreads();
+                if (cur >= k0 && tx < wact && ty < hact) {
+                    R Fmlo[NV], Fmhi[NV];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        Fmlo[q] = sFm[(size_t)((cur - 1) & 1) * NV * NT + (size_t)q * NT + tid];
+                        Fmhi[q] = sFm[(size_t)(cur & 1) * NV * NT + (size_t)q * NT + tid];
+                    }
+                    update_cell(cur, Fmlo, Fmhi);
+                }
+            } else {
+                __syncthreads();
+            }
+        }
     } else {
         R Fmlo[NV], Fmhi[NV];
 #pragma unroll
@@ -304,8 +422,16 @@ __device__ __forceinline__ void reduce_to_clock(Clock *clk, unsigned flags, unsi
     }
 }
 
+// Mixed path: cap registers at 64 per thread so that 1024 threads per SM stay
+// resident (two 512-thread CTAs); the all-FP64 path is limited by shared
+// memory instead.
+template <class R, int NT>
+struct MinBlocks {
+    static constexpr int value = std::is_same<R, float>::value ? (1024 / NT > 0 ? 1024 / NT : 1) : 1;
+};
+
 template <class R, int ND, int STAGE, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) stage_kernel(StageArgs a) {
+__global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) stage_kernel(StageArgs a) {
     using T = Tile<ND, TX, TY>;
     constexpr int NV = T::NV, PC = T::PC, NT = T::NT;
     constexpr int DM = ND - 1;
@@ -371,7 +497,7 @@ struct MultiArgs {
 };
 
 template <class R, int ND, int STAGE, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) multi_stage_kernel(MultiArgs a) {
+__global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) multi_stage_kernel(MultiArgs a) {
     using T = Tile<ND, TX, TY>;
     constexpr int NV = T::NV, PC = T::PC, NT = T::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
