@@ -50,7 +50,7 @@ template <> struct TileOf<double, 2> { static constexpr int TX = 128, TY = 1; };
 template <> struct TileOf<double, 3> { static constexpr int TX = 32, TY = 8; };
 template <> struct TileOf<float, 1> { static constexpr int TX = 256, TY = 1; };
 template <> struct TileOf<float, 2> { static constexpr int TX = 256, TY = 1; };
-template <> struct TileOf<float, 3> { static constexpr int TX = 32, TY = 16; };
+template <> struct TileOf<float, 3> { static constexpr int TX = 32, TY = 8; };
 
 template <class R, int ND, int STAGE>
 using StageOf = StageLaunch<R, ND, STAGE, TileOf<R, ND>::TX, TileOf<R, ND>::TY>;

@@ -28,10 +28,11 @@ __device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 max2(float2 a, float2 b) { return make_float2(a.x > b.x ? a.x : b.x, a.y > b.y ? a.y : b.y); }
 
+// minmod (Eq. 3): the smaller magnitude with the common sign, 0 if the signs
+// differ (or either is 0): min(|a|, |b|) carries the sign of a.
 __device__ __forceinline__ float minmod1(float a, float b) {
-    const bool same = (a > 0.f && b > 0.f) || (a < 0.f && b < 0.f);
-    if (!same) return 0.f;
-    return fabsf(a) < fabsf(b) ? a : b;
+    const float m = copysignf(fminf(fabsf(a), fabsf(b)), a);
+    return (__float_as_int(a) ^ __float_as_int(b)) >= 0 ? m : 0.f;
 }
 __device__ __forceinline__ float2 minmod2(float2 a, float2 b) { return make_float2(minmod1(a.x, b.x), minmod1(a.y, b.y)); }
 

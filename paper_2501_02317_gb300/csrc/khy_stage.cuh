@@ -92,6 +92,10 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
     const int wact = min(TX, g.n[0] - x0);
     const int hact = (ND == 3) ? min(TY, g.n[1] - y0) : 1;
 
+    // dt/dx and dt/(2 dx) rounded to FP32 once (they scale the small
+    // low-order part of the flux sums in the mixed update)
+    const float c32 = mx::d2f(dtdx[0]), hc32 = mx::d2f(0.5 * dtdx[0]);
+
     // tiles whose halo box lies inside the grid skip the ghost-zone index map
     const bool x_inside = x0 >= 2 && x0 + wact + 2 <= g.n[0];
     const bool y_inside = ND != 3 || (y0 >= 2 && y0 + hact + 2 <= g.n[1]);
@@ -226,10 +230,13 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
             }
             return true;
         };
-        for (int pr = tid; 2 * pr < ntask; pr += NT) {
+        // lane x of thread t takes task t, lane y task t + half: consecutive
+        // threads read consecutive shared-memory words (no bank conflicts)
+        const int half = (ntask + 1) / 2;
+        for (int pr = tid; pr < half; pr += NT) {
             Task ta, tb;
-            const bool va = decode(2 * pr, ta);
-            const bool vb = (2 * pr + 1 < ntask) && decode(2 * pr + 1, tb);
+            const bool va = decode(pr, ta);
+            const bool vb = (pr + half < ntask) && decode(pr + half, tb);
             if (!va && !vb) continue;
             if (!va) ta = tb;  // an idle lane recomputes its partner's face and stores nothing
             if (!vb) tb = ta;
@@ -290,11 +297,11 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
                     if (ND >= 2) S = mx::ff_add(S, Dm);
                     const double c = dtdx[0];
                     if (STAGE == 1) {
-                        const double lo = mx::f2d(__fmul_rn(mx::d2f(c), S.lo));
+                        const double lo = mx::f2d(__fmul_rn(c32, S.lo));
                         r = __fma_rn(c, mx::f2d(S.hi), __dadd_rn(u, lo));
                     } else {
                         const double hc = 0.5 * c;
-                        const double lo = mx::f2d(__fmul_rn(mx::d2f(hc), S.lo));
+                        const double lo = mx::f2d(__fmul_rn(hc32, S.lo));
                         const double A = __dadd_rn(Ubase[(long long)q * N + idx], u);
                         r = __fma_rn(hc, mx::f2d(S.hi), __fma_rn(0.5, A, lo));
                     }
