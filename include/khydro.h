@@ -53,7 +53,10 @@ typedef enum {
     KHY_ERR_BUDGET = -7        /* serving: the job does not fit the HBM budget */
 } khy_status;
 
-typedef enum { KHY_PREC_FP64 = 0, KHY_PREC_MIXED = 1 } khy_prec;
+/* Precision (Sec. 3.2.2): all-FP64; mixed (FP32 reconstruction and Riemann
+ * flux, FP64 conserved state); all-FP32 (FP32 state and flux: the paper's
+ * "Single", conservation to FP32 round-off; single grids only). */
+typedef enum { KHY_PREC_FP64 = 0, KHY_PREC_MIXED = 1, KHY_PREC_FP32 = 2 } khy_prec;
 
 /* Physical boundary rules of Sec. 3.1.1 plus periodic wrap, per axis side. */
 typedef enum {
@@ -161,7 +164,8 @@ khy_status khy_get_flags(khy_sim *sim, unsigned *flags, unsigned long long *floo
 typedef struct khy_batch khy_batch;
 
 /* Validates every descriptor (same ndim and prec for all), allocates the
- * pooled states and the clocks, binds the stream (NULL: a private stream)
+ * pooled states and the clocks, binds the stream (NULL: a private stream;
+ * KHY_PREC_FP64 or KHY_PREC_MIXED)
  * and builds the segment schedule for the tile variant remembered for this
  * batch shape (variant 0 if none was tuned).  Targets start at t_end = 0, so
  * nothing steps until khy_batch_set_target. */
@@ -281,8 +285,9 @@ khy_status khy_server_stats(khy_server *s, long *completed, int *active, int *qu
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture.  Every call shares the
  * array: calls whose work overlaps on the GPU (other streams or threads)
- * race.  Errors: KHY_ERR_ARG for an invalid descriptor, NULL pointers, NaN
- * times, or a state larger than the scratch (the message gives both sizes);
+ * race.  Errors: KHY_ERR_ARG for an invalid descriptor, KHY_PREC_FP32, NULL
+ * pointers, NaN times, or a state larger than the scratch (the message gives
+ * both sizes);
  * KHY_ERR_CUDA if a launch fails. */
 khy_status khy_step_noalloc(const khy_mesh_desc *desc, double *U_dev, double t, double t_end, double *out_dev,
                             void *cuda_stream);

@@ -4,6 +4,7 @@ The translation units are compiled in parallel and linked into one shared
 library:
   * khy_fp64.cu    -- all-FP64 kernels, -fmad=false (bitwise-reproducible)
   * khy_mixed.cu   -- mixed-precision kernels (FP32 flux, FP64 state)
+  * khy_single.cu  -- all-FP32 kernels (FP32 state and flux)
   * khy_runtime.cu -- C ABI, simulation objects, graphs, -fmad=false
   * khy_noalloc.cu -- the allocation-free one-step entry point
   * khy_batch.cu   -- many grids stepped together (batch engine)
@@ -33,6 +34,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
 UNITS = {
     "khy_fp64": ["-fmad=false"],
     "khy_mixed": [],
+    "khy_single": [],
     "khy_runtime": ["-fmad=false"],
     "khy_noalloc": ["-fmad=false"],
     "khy_batch": ["-fmad=false"],

@@ -17,6 +17,11 @@ cudaError_t launch_stage_fp64(const StageArgs &a, int stage, cudaStream_t s);
 cudaError_t launch_dt_fp64(const Geom &g, const double *U, Clock *clk, cudaStream_t s);
 cudaError_t launch_stage_mixed(const StageArgs &a, int stage, cudaStream_t s);
 cudaError_t launch_dt_mixed(const Geom &g, const double *U, Clock *clk, cudaStream_t s);
+// all-FP32 path (khy_single.cu): the state pointers in StageArgs and U point
+// to FP32 arrays (the buffers are reinterpreted)
+cudaError_t launch_stage_single(const StageArgs &a, int stage, cudaStream_t s);
+cudaError_t launch_dt_single(const Geom &g, const double *U, Clock *clk, cudaStream_t s);
+cudaError_t prepare_single(int ndim);
 
 // Many-grid (batched / served) launches.  A variant is a tile shape; the
 // variants of each dimensionality are listed by multi_variant_tile (the

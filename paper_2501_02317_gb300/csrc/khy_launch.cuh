@@ -9,7 +9,7 @@
 
 namespace khy {
 
-template <class R, int ND, int STAGE, int TX, int TY>
+template <class R, int ND, int STAGE, int TX, int TY, class S = double>
 struct StageLaunch {
     static int &resident() {  // resident CTAs on the device, 0 until prepared
         static int r = 0;
@@ -17,7 +17,7 @@ struct StageLaunch {
     }
     static cudaError_t prepare() {
         constexpr size_t smem = Tile<ND, TX, TY>::template smem_bytes<R>();
-        auto kern = stage_kernel<R, ND, STAGE, TX, TY>;
+        auto kern = stage_kernel<R, ND, STAGE, TX, TY, S>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per_sm = 0;
@@ -38,7 +38,7 @@ struct StageLaunch {
         const long long nm = (ND >= 2) ? a.g.n[ND - 1] : 1;
         const long long total = ntx * nty * nm;
         const int grid = (int)(total < resident() ? total : resident());
-        stage_kernel<R, ND, STAGE, TX, TY><<<grid, TX * TY, smem, s>>>(a);
+        stage_kernel<R, ND, STAGE, TX, TY, S><<<grid, TX * TY, smem, s>>>(a);
         return cudaGetLastError();
     }
 };
@@ -52,32 +52,32 @@ template <> struct TileOf<float, 1> { static constexpr int TX = 256, TY = 1; };
 template <> struct TileOf<float, 2> { static constexpr int TX = 256, TY = 1; };
 template <> struct TileOf<float, 3> { static constexpr int TX = 32, TY = 8; };
 
-template <class R, int ND, int STAGE>
-using StageOf = StageLaunch<R, ND, STAGE, TileOf<R, ND>::TX, TileOf<R, ND>::TY>;
+template <class R, int ND, int STAGE, class S = double>
+using StageOf = StageLaunch<R, ND, STAGE, TileOf<R, ND>::TX, TileOf<R, ND>::TY, S>;
 
-template <class R>
+template <class R, class S = double>
 static cudaError_t launch_stage_prec(const StageArgs &a, int stage, cudaStream_t s) {
     switch (a.g.ndim) {
-        case 1: return stage == 1 ? StageOf<R, 1, 1>::launch(a, s) : StageOf<R, 1, 2>::launch(a, s);
-        case 2: return stage == 1 ? StageOf<R, 2, 1>::launch(a, s) : StageOf<R, 2, 2>::launch(a, s);
-        case 3: return stage == 1 ? StageOf<R, 3, 1>::launch(a, s) : StageOf<R, 3, 2>::launch(a, s);
+        case 1: return stage == 1 ? StageOf<R, 1, 1, S>::launch(a, s) : StageOf<R, 1, 2, S>::launch(a, s);
+        case 2: return stage == 1 ? StageOf<R, 2, 1, S>::launch(a, s) : StageOf<R, 2, 2, S>::launch(a, s);
+        case 3: return stage == 1 ? StageOf<R, 3, 1, S>::launch(a, s) : StageOf<R, 3, 2, S>::launch(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <class R>
+template <class R, class S = double>
 static cudaError_t prepare_prec(int ndim) {
     cudaError_t e;
     switch (ndim) {
         case 1:
-            if ((e = StageOf<R, 1, 1>::prepare()) != cudaSuccess) return e;
-            return StageOf<R, 1, 2>::prepare();
+            if ((e = StageOf<R, 1, 1, S>::prepare()) != cudaSuccess) return e;
+            return StageOf<R, 1, 2, S>::prepare();
         case 2:
-            if ((e = StageOf<R, 2, 1>::prepare()) != cudaSuccess) return e;
-            return StageOf<R, 2, 2>::prepare();
+            if ((e = StageOf<R, 2, 1, S>::prepare()) != cudaSuccess) return e;
+            return StageOf<R, 2, 2, S>::prepare();
         case 3:
-            if ((e = StageOf<R, 3, 1>::prepare()) != cudaSuccess) return e;
-            return StageOf<R, 3, 2>::prepare();
+            if ((e = StageOf<R, 3, 1, S>::prepare()) != cudaSuccess) return e;
+            return StageOf<R, 3, 2, S>::prepare();
         default: return cudaErrorInvalidValue;
     }
 }
@@ -191,14 +191,14 @@ static cudaError_t launch_multi_dt_prec(const MultiArgs &a, int ndim, int v, int
     return cudaGetLastError();
 }
 
-template <class R>
+template <class R, class S = double>
 static cudaError_t launch_dt_prec(const Geom &g, const double *U, Clock *clk, cudaStream_t s) {
     const long long blocks_needed = (g.ncell + 255) / 256;
     const int blocks = (int)(blocks_needed < 152 * 8 ? blocks_needed : 152 * 8);
     switch (g.ndim) {
-        case 1: dt_kernel<R, 1><<<blocks, 256, 0, s>>>(g, U, clk); break;
-        case 2: dt_kernel<R, 2><<<blocks, 256, 0, s>>>(g, U, clk); break;
-        case 3: dt_kernel<R, 3><<<blocks, 256, 0, s>>>(g, U, clk); break;
+        case 1: dt_kernel<R, 1, S><<<blocks, 256, 0, s>>>(g, U, clk); break;
+        case 2: dt_kernel<R, 2, S><<<blocks, 256, 0, s>>>(g, U, clk); break;
+        case 3: dt_kernel<R, 3, S><<<blocks, 256, 0, s>>>(g, U, clk); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

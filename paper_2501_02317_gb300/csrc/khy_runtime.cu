@@ -80,6 +80,16 @@ __global__ void prim_to_cons_kernel(Geom g, const double *W, double *U) {
     }
 }
 
+// all-FP32 path: the state lives in FP32; the API's FP64 arrays are converted
+__global__ void to_float_kernel(const double *in, float *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+__global__ void to_double_kernel(const float *in, double *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
 // Error-free transformation a + b = s + e (Knuth TwoSum).
 __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
     s = a + b;
@@ -161,7 +171,8 @@ khy_status validate(const khy_mesh_desc *d) {
     if (ncell > (1LL << 31)) return fail(KHY_ERR_ARG, "too many cells (%lld > 2^31)", ncell);
     if (!(d->gamma > 1.0) || !std::isfinite(d->gamma)) return fail(KHY_ERR_ARG, "gamma must be > 1");
     if (!(d->cfl > 0.0 && d->cfl <= 1.0)) return fail(KHY_ERR_ARG, "cfl must be in (0, 1]");
-    if (d->prec != KHY_PREC_FP64 && d->prec != KHY_PREC_MIXED) return fail(KHY_ERR_ARG, "prec must be a khy_prec");
+    if (d->prec != KHY_PREC_FP64 && d->prec != KHY_PREC_MIXED && d->prec != KHY_PREC_FP32)
+        return fail(KHY_ERR_ARG, "prec must be a khy_prec");
     if (!(d->rho_floor >= 0.0) || !(d->p_floor >= 0.0)) return fail(KHY_ERR_ARG, "floors must be >= 0");
     return KHY_OK;
 }
@@ -212,9 +223,19 @@ cudaError_t launch_stage(const khy_sim *s, int stage) {
         a.Ubase = s->U;
         a.Uout = s->U;
     }
+    if (s->desc.prec == KHY_PREC_FP32) return launch_stage_single(a, stage, s->stream);
     return s->desc.prec == KHY_PREC_FP64 ? launch_stage_fp64(a, stage, s->stream)
                                          : launch_stage_mixed(a, stage, s->stream);
 }
+
+cudaError_t prepare_prec_of(const khy_sim *s) {
+    if (s->desc.prec == KHY_PREC_FP32) return prepare_single(s->desc.ndim);
+    return s->desc.prec == KHY_PREC_FP64 ? prepare_fp64(s->desc.ndim) : prepare_mixed(s->desc.ndim);
+}
+
+bool single_state(const khy_sim *s) { return s->desc.prec == KHY_PREC_FP32; }
+
+int conv_blocks(long long n) { return (int)std::min<long long>((n + 255) / 256, 152 * 8); }
 
 cudaError_t enqueue_one_step(const khy_sim *s) {
     clock_step_kernel<<<1, 1, 0, s->stream>>>(s->clk, s->geom);
@@ -226,7 +247,7 @@ cudaError_t enqueue_one_step(const khy_sim *s) {
 
 khy_status ensure_graph(khy_sim *s) {
     if (s->graph) return KHY_OK;
-    KHY_CUDA(s->desc.prec == KHY_PREC_FP64 ? prepare_fp64(s->desc.ndim) : prepare_mixed(s->desc.ndim));
+    KHY_CUDA(prepare_prec_of(s));
     cudaGraph_t g = nullptr;
     KHY_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = cudaSuccess;
@@ -254,8 +275,9 @@ khy_status ensure_wmin(khy_sim *s) {
     if (s->wmin_valid) return KHY_OK;
     clock_wmin_reset_kernel<<<1, 1, 0, s->stream>>>(s->clk);
     KHY_CUDA(cudaGetLastError());
-    KHY_CUDA(s->desc.prec == KHY_PREC_FP64 ? launch_dt_fp64(s->geom, s->U, s->clk, s->stream)
-                                           : launch_dt_mixed(s->geom, s->U, s->clk, s->stream));
+    if (s->desc.prec == KHY_PREC_FP32) KHY_CUDA(launch_dt_single(s->geom, s->U, s->clk, s->stream));
+    else KHY_CUDA(s->desc.prec == KHY_PREC_FP64 ? launch_dt_fp64(s->geom, s->U, s->clk, s->stream)
+                                                : launch_dt_mixed(s->geom, s->U, s->clk, s->stream));
     s->wmin_valid = true;
     return KHY_OK;
 }
@@ -362,7 +384,14 @@ khy_status khy_set_conserved_dev(khy_sim *s, const double *U_dev, size_t count) 
     if (!s || !U_dev) return fail(KHY_ERR_ARG, "NULL argument");
     khy_status st = check_count(s, count);
     if (st != KHY_OK) return st;
-    KHY_CUDA(cudaMemcpyAsync(s->U, U_dev, count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    if (single_state(s)) {
+        KHY_CUDA(cudaMemcpyAsync(s->U1, U_dev, count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+        to_float_kernel<<<conv_blocks((long long)count), 256, 0, s->stream>>>(s->U1, reinterpret_cast<float *>(s->U),
+                                                                           (long long)count);
+        KHY_CUDA(cudaGetLastError());
+    } else {
+        KHY_CUDA(cudaMemcpyAsync(s->U, U_dev, count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    }
     s->wmin_valid = false;
     return KHY_OK;
 }
@@ -371,7 +400,14 @@ khy_status khy_set_conserved(khy_sim *s, const double *U, size_t count) {
     if (!s || !U) return fail(KHY_ERR_ARG, "NULL argument");
     khy_status st = check_count(s, count);
     if (st != KHY_OK) return st;
-    KHY_CUDA(cudaMemcpyAsync(s->U, U, count * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    if (single_state(s)) {
+        KHY_CUDA(cudaMemcpyAsync(s->U1, U, count * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        to_float_kernel<<<conv_blocks((long long)count), 256, 0, s->stream>>>(s->U1, reinterpret_cast<float *>(s->U),
+                                                                           (long long)count);
+        KHY_CUDA(cudaGetLastError());
+    } else {
+        KHY_CUDA(cudaMemcpyAsync(s->U, U, count * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    }
     KHY_CUDA(cudaStreamSynchronize(s->stream));
     s->wmin_valid = false;
     return KHY_OK;
@@ -385,6 +421,12 @@ static khy_status convert_prim(khy_sim *s) {
         default: prim_to_cons_kernel<3><<<blocks, 256, 0, s->stream>>>(s->geom, s->U1, s->U); break;
     }
     KHY_CUDA(cudaGetLastError());
+    if (single_state(s)) {  // FP64 conserved values in U -> FP32 state (staged through U1)
+        const long long n = (long long)nvar_of(s->desc) * s->geom.ncell;
+        to_float_kernel<<<conv_blocks(n), 256, 0, s->stream>>>(s->U, reinterpret_cast<float *>(s->U1), n);
+        KHY_CUDA(cudaGetLastError());
+        KHY_CUDA(cudaMemcpyAsync(s->U, s->U1, n * sizeof(float), cudaMemcpyDeviceToDevice, s->stream));
+    }
     s->wmin_valid = false;
     return KHY_OK;
 }
@@ -465,7 +507,7 @@ khy_status khy_profile_steps(khy_sim *s, double t_end, long nsteps, float ms[3])
     if (nsteps < 1) return fail(KHY_ERR_ARG, "nsteps must be >= 1");
     khy_status st = check_periodic_pairs(s->desc);
     if (st != KHY_OK) return st;
-    KHY_CUDA(s->desc.prec == KHY_PREC_FP64 ? prepare_fp64(s->desc.ndim) : prepare_mixed(s->desc.ndim));
+    KHY_CUDA(prepare_prec_of(s));
     clock_target_kernel<<<1, 1, 0, s->stream>>>(s->clk, t_end, (long long)nsteps);
     KHY_CUDA(cudaGetLastError());
     if ((st = ensure_wmin(s)) != KHY_OK) return st;
@@ -506,7 +548,14 @@ khy_status khy_get_conserved(khy_sim *s, double *U, size_t count) {
     if (!s || !U) return fail(KHY_ERR_ARG, "NULL argument");
     khy_status st = check_count(s, count);
     if (st != KHY_OK) return st;
-    KHY_CUDA(cudaMemcpyAsync(U, s->U, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (single_state(s)) {
+        to_double_kernel<<<conv_blocks((long long)count), 256, 0, s->stream>>>(reinterpret_cast<const float *>(s->U),
+                                                                            s->U1, (long long)count);
+        KHY_CUDA(cudaGetLastError());
+        KHY_CUDA(cudaMemcpyAsync(U, s->U1, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    } else {
+        KHY_CUDA(cudaMemcpyAsync(U, s->U, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    }
     KHY_CUDA(cudaStreamSynchronize(s->stream));
     return KHY_OK;
 }
@@ -515,7 +564,13 @@ khy_status khy_get_conserved_dev(khy_sim *s, double *U_dev, size_t count) {
     if (!s || !U_dev) return fail(KHY_ERR_ARG, "NULL argument");
     khy_status st = check_count(s, count);
     if (st != KHY_OK) return st;
-    KHY_CUDA(cudaMemcpyAsync(U_dev, s->U, count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    if (single_state(s)) {
+        to_double_kernel<<<conv_blocks((long long)count), 256, 0, s->stream>>>(reinterpret_cast<const float *>(s->U),
+                                                                            U_dev, (long long)count);
+        KHY_CUDA(cudaGetLastError());
+    } else {
+        KHY_CUDA(cudaMemcpyAsync(U_dev, s->U, count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    }
     return KHY_OK;
 }
 
@@ -534,8 +589,15 @@ khy_status khy_totals(khy_sim *s, double out[5]) {
     const int nv = nvar_of(s->desc);
     const long long N = s->geom.ncell;
     const int blocks = (int)std::min<long long>((N + 255) / 256, kTotalsBlocks);
+    const double *src = s->U;
+    if (single_state(s)) {
+        to_double_kernel<<<conv_blocks((long long)nv * N), 256, 0, s->stream>>>(reinterpret_cast<const float *>(s->U),
+                                                                             s->U1, (long long)nv * N);
+        KHY_CUDA(cudaGetLastError());
+        src = s->U1;
+    }
     for (int q = 0; q < nv; ++q) {
-        totals_kernel<<<blocks, 256, 0, s->stream>>>(s->U + (long long)q * N, N, s->red);
+        totals_kernel<<<blocks, 256, 0, s->stream>>>(src + (long long)q * N, N, s->red);
         KHY_CUDA(cudaGetLastError());
         KHY_CUDA(cudaMemcpyAsync(s->red_host, s->red, sizeof(double) * 2 * blocks, cudaMemcpyDeviceToHost, s->stream));
         KHY_CUDA(cudaStreamSynchronize(s->stream));

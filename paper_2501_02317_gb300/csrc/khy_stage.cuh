@@ -38,6 +38,7 @@
 #include "khy_kernels.cuh"
 #include "khy_mixed_kernels.cuh"
 #include "khy_packed.cuh"
+#include "khy_single_kernels.cuh"
 
 namespace khy {
 
@@ -73,12 +74,16 @@ struct Tile {
 // Shared by the single-grid and the multi-grid kernels.  Accumulates the
 // status bits, the floor count and (stage 2) the CFL minimum into the
 // caller's registers.
-template <class R, int ND, int STAGE, int TX, int TY>
-__device__ __forceinline__ void run_segment(const Geom &g, const double *__restrict__ Uin, const double *Ubase,
-                                            double *Uout, const double (&dtdx)[3], int cubic, int x0, int y0,
+// S is the storage type of the conserved state: double (all-FP64 and mixed
+// paths) or float (all-FP32 path, S = R = float).
+template <class R, int ND, int STAGE, int TX, int TY, class S = double>
+__device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__ Uin, const S *Ubase,
+                                            S *Uout, const double (&dtdx)[3], int cubic, int x0, int y0,
                                             int k0, int k1, R *sW, R *sFx, R *sFy, unsigned &flags,
                                             unsigned &floors, double &wmin) {
     constexpr bool MIX = std::is_same<R, float>::value;
+    constexpr bool SINGLE = std::is_same<S, float>::value;
+    static_assert(!SINGLE || MIX, "an FP32 state needs FP32 fluxes");
     using T = Tile<ND, TX, TY>;
     constexpr int NV = T::NV, PX = T::PX, PC = T::PC, NT = T::NT;
     constexpr int DM = ND - 1;  // march axis (ND >= 2)
@@ -95,6 +100,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
     // dt/dx and dt/(2 dx) rounded to FP32 once (they scale the small
     // low-order part of the flux sums in the mixed update)
     const float c32 = mx::d2f(dtdx[0]), hc32 = mx::d2f(0.5 * dtdx[0]);
+    const float c32x = c32, c32y = mx::d2f(dtdx[1]), c32m = mx::d2f(dtdx[DM < 0 ? 0 : DM]);
 
     // tiles whose halo box lies inside the grid skip the ghost-zone index map
     const bool x_inside = x0 >= 2 && x0 + wact + 2 <= g.n[0];
@@ -122,15 +128,22 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
                 act[1] = actm;
             }
             const long long idx = ((long long)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
-            double u[NV];
             R w[NV];
-#pragma unroll
-            for (int q = 0; q < NV; ++q) u[q] = __ldg(Uin + (long long)q * N + idx);
             unsigned fl = 0;
-            if constexpr (MIX) {
-                mx::recover<ND>(u, mk, w, flags, fl);
+            if constexpr (SINGLE) {
+                float u[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) u[q] = __ldg(Uin + (long long)q * N + idx);
+                sg::recover<ND>(u, mk, w, flags, fl);
             } else {
-                recover<ND>(u, g, w, flags, fl);
+                double u[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) u[q] = __ldg(Uin + (long long)q * N + idx);
+                if constexpr (MIX) {
+                    mx::recover<ND>(u, mk, w, flags, fl);
+                } else {
+                    recover<ND>(u, g, w, flags, fl);
+                }
             }
             const bool interior = hx >= 2 && hx < TX + 2 && x0 - 2 + hx < g.n[0] &&
                                   (ND != 3 || (hy >= 2 && hy < TY + 2 && y0 - 2 + hy < g.n[1])) &&
@@ -271,12 +284,33 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
         const int gz = (ND == 3) ? cur : 0;
         if (gx >= g.n[0] || (ND == 3 && gy >= g.n[1])) return;
         const long long idx = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
+        if constexpr (SINGLE) {  // all-FP32: U + dt L(U) in FP32, directions in x, y, z order
+            float un[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                const float *fx = reinterpret_cast<const float *>(sFx) + (size_t)q * T::NXF + ty * (TX + 1) + tx;
+                const float *fy = reinterpret_cast<const float *>(sFy) + (size_t)q * T::NYF + ty * TX + tx;
+                float acc = __fmul_rn(c32x, __fsub_rn(fx[0], fx[1]));
+                if (ND == 3) acc = __fmaf_rn(c32y, __fsub_rn(fy[0], fy[TX]), acc);
+                if (ND >= 2) acc = __fmaf_rn(c32m, __fsub_rn((float)Fmlo[q], (float)Fmhi[q]), acc);
+                const float u = Uin[(long long)q * N + idx];
+                float r;
+                if (STAGE == 1) r = __fadd_rn(u, acc);
+                else r = __fmul_rn(0.5f, __fadd_rn(Ubase[(long long)q * N + idx], __fadd_rn(u, acc)));
+                un[q] = r;
+                Uout[(long long)q * N + idx] = r;
+            }
+            if (STAGE == 2) {
+                const double c = (double)sg::cfl_candidate<ND>(un, mk);
+                wmin = c < wmin ? c : wmin;
+            }
+        } else {
         double un[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
             const R *fx = sFx + (size_t)q * T::NXF + ty * (TX + 1) + tx;
             const R *fy = sFy + (size_t)q * T::NYF + ty * TX + tx;
-            const double u = Uin[(long long)q * N + idx];
+            const double u = (double)Uin[(long long)q * N + idx];
             double r;
             if constexpr (!MIX) {
                 // dU = -sum_d (dt/dx_d)(F_hi - F_lo), directions in x, y, z order
@@ -327,6 +361,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const double *__restr
                 c = cfl_candidate<ND>(w, g);
             }
             wmin = c < wmin ? c : wmin;
+        }
         }
     };
 
@@ -437,7 +472,7 @@ struct MinBlocks {
     static constexpr int value = std::is_same<R, float>::value ? (1024 / NT > 0 ? 1024 / NT : 1) : 1;
 };
 
-template <class R, int ND, int STAGE, int TX, int TY>
+template <class R, int ND, int STAGE, int TX, int TY, class S = double>
 __global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) stage_kernel(StageArgs a) {
     using T = Tile<ND, TX, TY>;
     constexpr int NV = T::NV, PC = T::PC, NT = T::NT;
@@ -468,8 +503,9 @@ __global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) stage_ke
         const int x0 = (int)(tile % ntx) * TX;
         const int y0 = (ND == 3) ? (int)(tile / ntx) * TY : 0;
         pos += k1 - k0;
-        run_segment<R, ND, STAGE, TX, TY>(g, a.Uin, a.Ubase, a.Uout, dtdx, a.cubic, x0, y0, k0, k1, sW, sFx, sFy,
-                                          flags, floors, wmin);
+        run_segment<R, ND, STAGE, TX, TY, S>(g, reinterpret_cast<const S *>(a.Uin), reinterpret_cast<const S *>(a.Ubase),
+                                             reinterpret_cast<S *>(a.Uout), dtdx, a.cubic, x0, y0, k0, k1, sW, sFx,
+                                             sFy, flags, floors, wmin);
     }
     reduce_to_clock<STAGE, NT>(a.clk, flags, floors, wmin);
 }
@@ -573,24 +609,35 @@ __global__ void __launch_bounds__(256) multi_dt_kernel(MultiArgs a, int TX, int 
 
 // CFL minimum over all cells of U (used when the state was set from outside);
 // the same per-cell candidate as the fused one in stage_kernel<..., 2, ...>.
-template <class R, int ND>
+template <class R, int ND, class S = double>
 __global__ void __launch_bounds__(256) dt_kernel(Geom g, const double *U, Clock *clk) {
     constexpr bool MIX = std::is_same<R, float>::value;
+    constexpr bool SINGLE = std::is_same<S, float>::value;
     constexpr int NV = ND + 2;
     const mx::MixConsts mk = mx::make_mix(g);
     const long long N = g.ncell;
     unsigned flags = 0, floors = 0;
     double wmin = __longlong_as_double((long long)kInfBits);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        double u[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) u[q] = U[(long long)q * N + c];
         double m;
-        if constexpr (MIX) {
+        if constexpr (SINGLE) {
+            const float *Uf = reinterpret_cast<const float *>(U);
+            float u[NV], w[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) u[q] = Uf[(long long)q * N + c];
+            sg::recover<ND>(u, mk, w, flags, floors);
+            m = (double)sg::cfl_candidate<ND>(u, mk);
+        } else if constexpr (MIX) {
+            double u[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) u[q] = U[(long long)q * N + c];
             float w[NV];
             mx::recover<ND>(u, mk, w, flags, floors);
             m = mx::f2d(mx::cfl_candidate<ND>(u, mk));
         } else {
+            double u[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) u[q] = U[(long long)q * N + c];
             double w[NV];
             recover<ND>(u, g, w, flags, floors);
             m = cfl_candidate<ND>(w, g);

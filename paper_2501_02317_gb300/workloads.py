@@ -33,6 +33,7 @@ BC_REFLECT = 3
 
 PREC_FP64 = 0
 PREC_MIXED = 1
+PREC_FP32 = 2
 
 DEFAULT_FLOOR = 1e-10
 

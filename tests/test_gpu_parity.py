@@ -284,3 +284,45 @@ def test_dt_matches_oracle():
     _, _, dt_o, _ = oracle.heun_step(mesh, U0, 0.0, 1.0)
     _, t, s, dt = gpu_run(mesh, W, max_steps=1)
     assert dt == dt_o and t == dt_o
+
+
+# ------------------------------------------------------------ all-FP32 path (paper's "Single")
+
+SINGLE_TOL = 1e-4
+
+
+@pytest.mark.parametrize("case", ["kh128", "turb32", "sod512", "jumpy3d"])
+def test_single_precision_path(case):
+    if case == "kh128":
+        mesh, W = wl.kelvin_helmholtz(128, prec=wl.PREC_FP32)
+        steps, tol = 30, SINGLE_TOL
+    elif case == "turb32":
+        mesh, W = wl.turbulence(32, prec=wl.PREC_FP32)
+        steps, tol = 20, SINGLE_TOL
+    elif case == "sod512":
+        mesh, W = wl.sod(512, prec=wl.PREC_FP32)
+        steps, tol = 1 << 30, 1e-3
+    else:
+        mesh = wl.Mesh(ndim=3, n=(37, 11, 9), gamma=5.0 / 3.0, cfl=0.3, prec=wl.PREC_FP32)
+        W = wl.random_jumpy(mesh, seed=3)
+        steps, tol = 4, SINGLE_TOL
+    t_end = 0.2 if case == "sod512" else 1e30
+    Uo, to, so, _ = oracle_run(mesh, W, t_end, max_steps=steps)
+    U, t, s, _ = gpu_run(mesh, W, t_end, max_steps=-1 if case == "sod512" else steps)
+    errs = field_errors(mesh, U, Uo)
+    assert errs[0] <= tol and errs[-1] <= tol, errs
+
+
+def test_single_precision_conservation():
+    from paper_2501_02317_gb300 import khydro
+    mesh = wl.Mesh(ndim=3, n=(40, 24, 36), gamma=5.0 / 3.0, cfl=0.3, prec=wl.PREC_FP32)
+    W = wl.random_jumpy(mesh, seed=4)
+    with khydro.Sim(mesh) as sim:
+        sim.set_primitive(W)
+        prev = sim.totals()
+        scale = np.abs(sim.conserved()).reshape(mesh.nvar, -1).sum(axis=1)
+        for _ in range(5):
+            sim.step_to(1e30, 1)
+            cur = sim.totals()
+            assert np.all(np.abs(cur - prev) / scale <= 1e-6), (cur - prev) / scale
+            prev = cur
