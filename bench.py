@@ -4,7 +4,8 @@ Default workload: 3D periodic turbulence box 256^3 (rho = 1, p = 0.6,
 random-phase Gaussian velocity field with a k^-4 shell spectrum, rms Mach 1),
 mixed precision (FP32 reconstruction/HLLC, FP64 state), CFL 0.3.  One
 benchmark step = one Heun step of the whole grid = ncell cell-updates.
-The same grid is also timed on the all-FP64 path.
+The same grid is also timed on the all-FP64 path, the all-FP32 path and
+with the memory-optimized van Leer integrator (mixed).
 
 Prints ONE JSON line.  ``--impl reference`` times the CPU oracle instead (the
 reference arm: a plain FP64 C program on the host cores).
@@ -33,6 +34,11 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s (mixed vs FP64, 1 GB300, % HBM roofline); p99 solve latency"
 UNIT = "cell-updates/s"
 BYTES_PER_CELL_UPDATE_3D = 200  # stage 1: read Un, write U1; stage 2: read U1 and Un, write Un+1 (5 x 8 B each)
+# all-FP32 Heun: the same five array passes of 5 x 4 B
+BYTES_PER_CELL_UPDATE_3D_FP32 = 100
+# van Leer, mixed: predictor reads Un (40 B), writes W (5 x 4 B); corrector
+# reads W and Un, writes Un+1
+BYTES_PER_CELL_UPDATE_3D_VL2 = 160
 
 
 def _recorded_traffic(workload: str):
@@ -332,6 +338,25 @@ def main():
     ms64 = sim64.profile_steps(T_END, 2)
     sim64.close()
 
+    # ---------------------------------------------------------- all-FP32 path, van Leer (mixed)
+    def leg(prec, integrator, k, bytes_per_cu):
+        m = mesh.replace(prec=prec, integrator=integrator)
+        s = khydro.Sim(m, stream=stream.cuda_stream)
+        s.set_primitive(W)
+        s.enqueue_steps(T_END, 3)
+        torch.cuda.synchronize()
+        t = max_over_ranks(timed_steps(s, k))
+        pm = s.profile_steps(T_END, 3)
+        state_bytes = s.device_bytes()[0]
+        s.close()
+        ach = bytes_per_cu * ncell / ((pm[1] + pm[2]) * 1e-3) / 1e9
+        return {"value": world * ncell * k / t, "unit": UNIT, "steps": k, "ms_per_step": 1e3 * t / k,
+                "stage_ms": [pm[1], pm[2]], "state_bytes": state_bytes, "bytes_per_cell_update": bytes_per_cu,
+                "hbm_achieved_gbs": ach, "hbm_frac": ach / peak_gbs}
+
+    fp32 = leg(wl.PREC_FP32, wl.INT_HEUN, K, BYTES_PER_CELL_UPDATE_3D_FP32)
+    vl2 = leg(wl.PREC_MIXED, wl.INT_VL2, K, BYTES_PER_CELL_UPDATE_3D_VL2)
+
     # ---------------------------------------------------------- end to end (host buffers)
     e2e = None
     if not args.no_e2e:
@@ -371,6 +396,8 @@ def main():
             "fp64": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": 1e3 * el64 / k64,
                      "stage_ms": [ms64[1], ms64[2]]},
             "mixed_over_fp64": value / value64,
+            "fp32": dict(fp32, workload="turbulence-3d-%d^3-fp32 (FP32 state and flux)" % args.n),
+            "vl2_mixed": dict(vl2, workload="turbulence-3d-%d^3-mixed, memory-optimized van Leer integrator" % args.n),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                          "frac": achieved / peak_gbs,
                          "traffic": _recorded_traffic("turbulence-3d-%d^3-mixed" % args.n),
@@ -384,6 +411,7 @@ def main():
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": 3 * K,
+            "gpu_launches_note": "timed region of the headline: clock + stage 1 + stage 2 per step",
             "status_flags": flags, "floor_hits": floors,
         }
         print(json.dumps(line), flush=True)

@@ -9,9 +9,10 @@
  * minmod-limited piecewise-linear reconstruction (Eq. 3, Sec. 3.2.2), the
  * HLLC Riemann flux with the subtraction-safe wave speeds (Eq. 4, Eq. 5,
  * Sec. 3.2.2) and the conservative update inside the Heun predictor-corrector
- * (Sec. 3.3).  Two precisions: all-FP64, and mixed (FP32 reconstruction and
- * Riemann flux, FP64 conserved state, recovery and flux-difference
- * accumulation; Sec. 3.2.2).
+ * or the memory-optimized van Leer predictor-corrector (Sec. 3.3).  Three
+ * precisions: all-FP64; mixed (FP32 reconstruction and Riemann flux, FP64
+ * conserved state, recovery and flux-difference accumulation; Sec. 3.2.2);
+ * all-FP32.
  *
  * Conventions for every call:
  *   - Every call returns a khy_status; nothing throws across the ABI.
@@ -66,8 +67,22 @@ typedef enum {
     KHY_BC_REFLECT = 3   /* mirror the interior, normal velocity negated */
 } khy_bc;
 
+/* Time integrator (Sec. 3.3).
+ *   KHY_INT_HEUN: U^1 = U^n + dt L(U^n); U^{n+1} = (U^n + (U^1 + dt L(U^1))) / 2.
+ *   KHY_INT_VL2 : memory-optimized van Leer predictor-corrector: the
+ *                 predictor U^{n+1/2} = U^n + (dt/2) L_1(U^n) uses first-order
+ *                 (piecewise-constant) face states and only its primitives
+ *                 W^{n+1/2} are kept, in the flux precision (FP32 in the mixed
+ *                 path); the corrector U^{n+1} = U^n + dt L(W^{n+1/2}) uses PLM
+ *                 face states of W^{n+1/2}.  The second state array (U^1, FP64)
+ *                 becomes a primitive array (FP32 in the mixed and FP32 paths),
+ *                 and the result is U^n plus flux differences only, so it is
+ *                 conservative to round-off.  Single grids only. */
+typedef enum { KHY_INT_HEUN = 0, KHY_INT_VL2 = 1 } khy_integrator;
+
 /* Mesh and method parameters.  n[d] >= 2 for d < ndim and n[d] == 1 for
- * d >= ndim; hi[d] > lo[d]; gamma > 1; 0 < cfl <= 1; floors >= 0. */
+ * d >= ndim; hi[d] > lo[d]; gamma > 1; 0 < cfl <= 1; floors >= 0.  A zeroed
+ * integrator field selects Heun. */
 typedef struct khy_mesh_desc {
     int ndim;         /* 1, 2 or 3 */
     int n[3];         /* interior cells per axis */
@@ -77,6 +92,7 @@ typedef struct khy_mesh_desc {
     double cfl;       /* Courant number C of dt = C min dx_d / (|v_d| + c_s) */
     int prec;         /* khy_prec */
     int bc[3][2];     /* khy_bc per axis, [0] = low side, [1] = high side */
+    int integrator;   /* khy_integrator */
     double rho_floor; /* floor on the recovered density (primitive only) */
     double p_floor;   /* floor on the recovered pressure (primitive only) */
 } khy_mesh_desc;
@@ -85,8 +101,9 @@ typedef struct khy_sim khy_sim;
 
 /* ------------------------------------------------------------ single grid */
 
-/* Validates *desc, allocates the state (U^n, U^1) and the device clock on the
- * current CUDA device, and binds the stream (cudaStream_t, may be NULL).
+/* Validates *desc, allocates the state (U^n, and U^1 or the van Leer
+ * primitives W^{n+1/2}) and the device clock on the current CUDA device, and
+ * binds the stream (cudaStream_t, may be NULL).
  * On success *out receives the simulation, time t = 0, state zero.
  * Errors: KHY_ERR_ARG (invalid desc), KHY_ERR_OOM, KHY_ERR_CUDA. */
 khy_status khy_create(const khy_mesh_desc *desc, void *cuda_stream, khy_sim **out);
@@ -114,24 +131,25 @@ khy_status khy_set_primitive_dev(khy_sim *sim, const double *W_dev, size_t count
 /* Sets the simulation time t. */
 khy_status khy_set_time(khy_sim *sim, double t);
 
-/* Advances by Heun steps (Sec. 3.3) until t reaches t_end or max_steps steps
- * were taken (max_steps < 0: no limit).  Each step: dt = C min over cells and
- * directions of dx_d/(|v_d| + c_s) from U^n (first sub-step only, Sec. 3.1),
- * clipped so that the last step lands on t_end; U^1 = U^n + dt L(U^n);
- * U^{n+1} = (U^n + (U^1 + dt L(U^1))) / 2.  The loop runs on the device in
+/* Advances by steps of the descriptor's integrator (Sec. 3.3) until t reaches
+ * t_end or max_steps steps were taken (max_steps < 0: no limit).  Each step:
+ * dt = C min over cells and directions of dx_d/(|v_d| + c_s) from U^n (first
+ * sub-step only, Sec. 3.1), clipped so that the last step lands on t_end;
+ * then the two sub-steps of khy_integrator.  The loop runs on the device in
  * captured CUDA graphs; the host polls a device flag between graph chunks.
  * steps_taken / t_out may be NULL.  Synchronises the stream. */
 khy_status khy_step_to(khy_sim *sim, double t_end, long max_steps, long *steps_taken, double *t_out);
 
-/* Enqueues exactly nsteps Heun steps toward t_end on the stream without any
+/* Enqueues exactly nsteps steps toward t_end on the stream without any
  * host synchronisation (steps past t_end are no-ops on the device).  Used for
  * timing and for overlapping several simulations. */
 khy_status khy_enqueue_steps(khy_sim *sim, double t_end, long nsteps);
 
-/* Profiling: enqueues nsteps Heun steps toward t_end without graphs, with a
+/* Profiling: enqueues nsteps steps toward t_end without graphs, with a
  * CUDA event pair around each launch, synchronises, and writes the average
- * duration in milliseconds of the clock launch (ms[0]), the stage-1 launch
- * (ms[1]) and the stage-2 launch (ms[2]).  nsteps >= 1. */
+ * duration in milliseconds of the clock launch (ms[0]), the first sub-step
+ * launch (ms[1]: Heun stage 1 or van Leer predictor) and the second (ms[2]).
+ * nsteps >= 1. */
 khy_status khy_profile_steps(khy_sim *sim, double t_end, long nsteps, float ms[3]);
 
 /* Copies the conserved state to host U (count doubles).  Synchronises. */
@@ -151,6 +169,11 @@ khy_status khy_totals(khy_sim *sim, double out[5]);
  * applied) and the number of floor applications; clears them when clear != 0. */
 khy_status khy_get_flags(khy_sim *sim, unsigned *flags, unsigned long long *floor_hits, int clear);
 
+/* Device memory held by the simulation, in bytes: *state_bytes for the two
+ * state arrays (U^n and U^1, or U^n and W^{n+1/2}), *total_bytes including
+ * the clock and reduction buffers.  Either pointer may be NULL. */
+khy_status khy_device_bytes(khy_sim *sim, size_t *state_bytes, size_t *total_bytes);
+
 /* ------------------------------------------------------------ many grids */
 
 /* A batch: many independent grids of one dimensionality and one precision,
@@ -163,9 +186,9 @@ khy_status khy_get_flags(khy_sim *sim, unsigned *flags, unsigned long long *floo
  * equal to the same grid stepped alone with khy_step_to. */
 typedef struct khy_batch khy_batch;
 
-/* Validates every descriptor (same ndim and prec for all), allocates the
- * pooled states and the clocks, binds the stream (NULL: a private stream;
- * KHY_PREC_FP64 or KHY_PREC_MIXED)
+/* Validates every descriptor (same ndim and prec for all; KHY_PREC_FP64 or
+ * KHY_PREC_MIXED; KHY_INT_HEUN), allocates the pooled states and the clocks,
+ * binds the stream (NULL: a private stream)
  * and builds the segment schedule for the tile variant remembered for this
  * batch shape (variant 0 if none was tuned).  Targets start at t_end = 0, so
  * nothing steps until khy_batch_set_target. */
@@ -232,7 +255,7 @@ khy_status khy_server_create(size_t hbm_budget_bytes, int max_slots, void *cuda_
  * frees everything. */
 void khy_server_destroy(khy_server *s);
 
-/* Queues a job: mesh desc (ndim 2 or 3, KHY_PREC_MIXED), primitive initial
+/* Queues a job: mesh desc (ndim 2 or 3, KHY_PREC_MIXED, KHY_INT_HEUN), primitive initial
  * state W (host, count = nvar*ncell doubles, copied), target time t_end > 0.
  * *job_id receives the job's id.  KHY_ERR_BUDGET if the job's two states
  * cannot fit the arena even when it is empty. */
@@ -285,8 +308,8 @@ khy_status khy_server_stats(khy_server *s, long *completed, int *active, int *qu
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture.  Every call shares the
  * array: calls whose work overlaps on the GPU (other streams or threads)
- * race.  Errors: KHY_ERR_ARG for an invalid descriptor, KHY_PREC_FP32, NULL
- * pointers, NaN times, or a state larger than the scratch (the message gives
+ * race.  Errors: KHY_ERR_ARG for an invalid descriptor, KHY_PREC_FP32,
+ * KHY_INT_VL2, NULL pointers, NaN times, or a state larger than the scratch (the message gives
  * both sizes);
  * KHY_ERR_CUDA if a launch fails. */
 khy_status khy_step_noalloc(const khy_mesh_desc *desc, double *U_dev, double t, double t_end, double *out_dev,

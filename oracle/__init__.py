@@ -73,6 +73,10 @@ def lib():
         L.orc_heun_step.restype = d
         L.orc_run.argtypes = [P(_OrcMesh), vp, P(d), d, ctypes.c_long, P(ctypes.c_uint)]
         L.orc_run.restype = ctypes.c_long
+        L.orc_vl2_step.argtypes = [P(_OrcMesh), vp, P(d), d, P(ctypes.c_uint)]
+        L.orc_vl2_step.restype = d
+        L.orc_run_with.argtypes = [P(_OrcMesh), vp, P(d), d, ctypes.c_long, ctypes.c_int, P(ctypes.c_uint)]
+        L.orc_run_with.restype = ctypes.c_long
         L.orc_totals.argtypes = [P(_OrcMesh), vp, vp]
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_set_threads.restype = ctypes.c_int
@@ -162,12 +166,25 @@ def heun_step(mesh, U: np.ndarray, t: float, t_end: float):
     return U, tt.value, dt, f.value
 
 
-def run(mesh, U: np.ndarray, t: float, t_end: float, max_steps: int = 1 << 40):
-    """Steps from t to t_end (or max_steps); returns (U, t, steps, flags)."""
+def vl2_step(mesh, U: np.ndarray, t: float, t_end: float):
+    """One memory-optimized van Leer step on a copy; returns (U_new, t_new, dt, flags)."""
     U = _arr(U, mesh.shape).copy()
     tt = ctypes.c_double(t)
     f = ctypes.c_uint(0)
-    s = lib().orc_run(ctypes.byref(_mesh(mesh)), _p(U), ctypes.byref(tt), float(t_end), int(max_steps), ctypes.byref(f))
+    dt = lib().orc_vl2_step(ctypes.byref(_mesh(mesh)), _p(U), ctypes.byref(tt), float(t_end), ctypes.byref(f))
+    return U, tt.value, dt, f.value
+
+
+def run(mesh, U: np.ndarray, t: float, t_end: float, max_steps: int = 1 << 40, integrator=None):
+    """Steps from t to t_end (or max_steps) with the mesh's integrator (0 Heun,
+    1 van Leer) unless one is given; returns (U, t, steps, flags)."""
+    if integrator is None:
+        integrator = getattr(mesh, "integrator", 0)
+    U = _arr(U, mesh.shape).copy()
+    tt = ctypes.c_double(t)
+    f = ctypes.c_uint(0)
+    s = lib().orc_run_with(ctypes.byref(_mesh(mesh)), _p(U), ctypes.byref(tt), float(t_end), int(max_steps),
+                           int(integrator), ctypes.byref(f))
     return U, tt.value, s, f.value
 
 

@@ -19,7 +19,8 @@
  *   - the HLLC Riemann solver with the contact speed of Eq. 4 and the
  *     subtraction-safe wave speeds of Eq. 5 (Sec. 3.2.2)
  *   - the conservative flux-difference update inside the Heun (RK2)
- *     predictor-corrector (Sec. 3.3)
+ *     predictor-corrector (Sec. 3.3), or inside the memory-optimized van Leer
+ *     predictor-corrector (Sec. 3.3, last paragraph)
  *
  * Readings where the paper is silent (each one is listed in the design notes):
  *   - HLLC p* estimate: the pressure-based (PVRS) estimate clamped at 0, the
@@ -36,6 +37,11 @@
  *     the product, so it cannot underflow.
  *   - dt = C * min over cells and directions of dx_d / (|v_d| + c_s), computed
  *     from U^n before stage 1, reused by stage 2, clipped to hit t_end.
+ *   - van Leer integrator (the paper names it only): the predictor advances
+ *     U^n by dt/2 with first-order (piecewise-constant) face states, and only
+ *     the primitives of that half-step state are kept; the corrector advances
+ *     U^n by the full dt with PLM face states of those primitives.  The final
+ *     state is U^n plus flux differences only, so it is conservative.
  *   - floors rho_floor, p_floor act on the recovered primitives only.
  *
  * Canonical operation order.  Every floating-point operation below is written
@@ -316,8 +322,10 @@ static void fill_ghosts_axis(const orc_mesh *m, const pad_t *P, double *Wp, int 
 /* --------------------------------------------- one stage right-hand side */
 
 /* dU = -sum_d (dt/dx_d) (F_{i+1/2} - F_{i-1/2}), directions summed x, y, z.
- * Each direction term is (F_hi - F_lo) first, then times dt/dx_d. */
-void orc_rhs(const orc_mesh *m, const double *U, double dt, double *dU, unsigned *flags) {
+ * Each direction term is (F_hi - F_lo) first, then times dt/dx_d.  The face
+ * states are the PLM states (order 2) or the two adjacent cell values
+ * themselves (order 1, the van Leer predictor). */
+static void rhs_order(const orc_mesh *m, const double *U, double dt, int order, double *dU, unsigned *flags) {
     const long N = ncell(m);
     const int nd = m->ndim, nv = 2 + nd;
     const pad_t P = make_pad(m);
@@ -376,6 +384,11 @@ void orc_rhs(const orc_mesh *m, const double *U, double dt, double *dU, unsigned
                             s[o][4] = Wp[(long)4 * NP + pc];
                         }
                         for (int q = 0; q < 5; ++q) {
+                            if (order == 1) {
+                                wl[q] = s[1][q];
+                                wr[q] = s[2][q];
+                                continue;
+                            }
                             /* left state: cell fc-1 at its upper face */
                             double sl = orc_minmod(s[1][q] - s[0][q], s[2][q] - s[1][q]);
                             wl[q] = s[1][q] + 0.5 * sl;
@@ -407,6 +420,10 @@ void orc_rhs(const orc_mesh *m, const double *U, double dt, double *dU, unsigned
     if (flags) *flags |= f;
 }
 
+void orc_rhs(const orc_mesh *m, const double *U, double dt, double *dU, unsigned *flags) {
+    rhs_order(m, U, dt, 2, dU, flags);
+}
+
 /* --------------------------------------------- Sec. 3.3: one Heun step */
 
 /* Advances U in place by one Heun step and t by dt.  dt comes from U^n
@@ -434,15 +451,53 @@ double orc_heun_step(const orc_mesh *m, double *U, double *t, double t_end, unsi
     return dt;
 }
 
-/* Steps until t reaches t_end or max_steps steps were taken.  Returns the
- * number of steps; *t is updated. */
-long orc_run(const orc_mesh *m, double *U, double *t, double t_end, long max_steps, unsigned *flags) {
+/* ------------------------------ Sec. 3.3: one memory-optimized van Leer step */
+
+/* Advances U in place by one van Leer predictor-corrector step and t by dt
+ * (dt from U^n as in orc_heun_step).
+ *   predictor: U^{n+1/2} = U^n + (dt/2) L_1(U^n), first-order face states;
+ *              only its primitives W^{n+1/2} are used afterwards
+ *   corrector: U^{n+1} = U^n + dt L_2(W^{n+1/2}), PLM face states
+ * Returns the dt used. */
+double orc_vl2_step(const orc_mesh *m, double *U, double *t, double t_end, unsigned *flags) {
+    const long NV = (long)(2 + m->ndim) * ncell(m);
+    double dt = orc_cfl_dt(m, U, flags);
+    int last = 0;
+    double rem = t_end - *t;
+    if (dt >= rem) { dt = rem; last = 1; }
+    double *dU = (double *)malloc(sizeof(double) * (size_t)NV);
+    double *Uh = (double *)malloc(sizeof(double) * (size_t)NV);
+    /* predictor: half step with piecewise-constant face states */
+    rhs_order(m, U, 0.5 * dt, 1, dU, flags);
+#pragma omp parallel for schedule(static)
+    for (long q = 0; q < NV; ++q) Uh[q] = U[q] + dU[q];
+    /* corrector: PLM on the primitives of U^{n+1/2} (rhs_order recovers them,
+     * floors included), full step from U^n */
+    rhs_order(m, Uh, dt, 2, dU, flags);
+#pragma omp parallel for schedule(static)
+    for (long q = 0; q < NV; ++q) U[q] = U[q] + dU[q];
+    *t = last ? t_end : *t + dt;
+    free(dU);
+    free(Uh);
+    return dt;
+}
+
+/* Steps with the given integrator (0 Heun, 1 van Leer) until t reaches t_end
+ * or max_steps steps were taken.  Returns the number of steps; *t is updated. */
+long orc_run_with(const orc_mesh *m, double *U, double *t, double t_end, long max_steps, int integrator,
+                  unsigned *flags) {
     long s = 0;
     while (*t < t_end && s < max_steps) {
-        orc_heun_step(m, U, t, t_end, flags);
+        if (integrator == 1) orc_vl2_step(m, U, t, t_end, flags);
+        else orc_heun_step(m, U, t, t_end, flags);
         ++s;
     }
     return s;
+}
+
+/* Heun steps until t reaches t_end or max_steps steps were taken. */
+long orc_run(const orc_mesh *m, double *U, double *t, double t_end, long max_steps, unsigned *flags) {
+    return orc_run_with(m, U, t, t_end, max_steps, 0, flags);
 }
 
 /* ------------------------------------ conservation totals (diagnostic) */

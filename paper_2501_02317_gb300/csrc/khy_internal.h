@@ -10,7 +10,8 @@
 
 namespace khy {
 
-// Stage kernel (stage = 1 or 2) and CFL-minimum kernel for each precision.
+// Stage kernel (stage 1, 2: Heun; 3, 4: van Leer predictor and corrector)
+// and CFL-minimum kernel for each precision.
 // khy_fp64.cu builds the double instantiations with -fmad=false; khy_mixed.cu
 // builds the float (mixed) instantiations.
 cudaError_t launch_stage_fp64(const StageArgs &a, int stage, cudaStream_t s);

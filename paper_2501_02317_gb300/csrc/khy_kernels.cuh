@@ -278,7 +278,9 @@ __device__ __forceinline__ void hllc(const Consts<R> &k, const R (&wl)[NT + 3], 
 // Minmod PLM per primitive (undivided differences: minmod is positively
 // homogeneous, so the dx factors of the slope cancel), then HLLC in the frame
 // rotated onto dir.  F is returned in conserved order (mass, m_0.., E).
-template <int ND, class R>
+// PLM = false: first-order face states (the two adjacent cells themselves),
+// as in the predictor of the van Leer integrator (Sec. 3.3).
+template <int ND, class R, bool PLM = true>
 __device__ __forceinline__ void face_flux(const R (&s)[4][ND + 2], int dir, const Consts<R> &k, R (&F)[ND + 2]) {
     constexpr int NT = ND - 1;
     // rotation: storage slot of rotated component j (0 rho, 1 normal, 2.. transverse, last p)
@@ -293,6 +295,11 @@ __device__ __forceinline__ void face_flux(const R (&s)[4][ND + 2], int dir, cons
     for (int j = 0; j < ND + 2; ++j) {
         const int q = slot[j];
         const R s0 = s[0][q], s1 = s[1][q], s2 = s[2][q], s3 = s[3][q];
+        if (!PLM) {
+            wl[j] = s1;
+            wr[j] = s2;
+            continue;
+        }
         const R a = minmod<R>(rsub(s1, s0), rsub(s2, s1));
         wl[j] = radd(s1, rmul(R(0.5), a));
         const R b = minmod<R>(rsub(s2, s1), rsub(s3, s2));

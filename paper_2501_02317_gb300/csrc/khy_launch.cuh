@@ -55,29 +55,43 @@ template <> struct TileOf<float, 3> { static constexpr int TX = 32, TY = 8; };
 template <class R, int ND, int STAGE, class S = double>
 using StageOf = StageLaunch<R, ND, STAGE, TileOf<R, ND>::TX, TileOf<R, ND>::TY, S>;
 
-template <class R, class S = double>
-static cudaError_t launch_stage_prec(const StageArgs &a, int stage, cudaStream_t s) {
-    switch (a.g.ndim) {
-        case 1: return stage == 1 ? StageOf<R, 1, 1, S>::launch(a, s) : StageOf<R, 1, 2, S>::launch(a, s);
-        case 2: return stage == 1 ? StageOf<R, 2, 1, S>::launch(a, s) : StageOf<R, 2, 2, S>::launch(a, s);
-        case 3: return stage == 1 ? StageOf<R, 3, 1, S>::launch(a, s) : StageOf<R, 3, 2, S>::launch(a, s);
+template <class R, int ND, class S>
+static cudaError_t launch_stage_nd(const StageArgs &a, int stage, cudaStream_t s) {
+    switch (stage) {
+        case 1: return StageOf<R, ND, 1, S>::launch(a, s);
+        case 2: return StageOf<R, ND, 2, S>::launch(a, s);
+        case 3: return StageOf<R, ND, 3, S>::launch(a, s);
+        case 4: return StageOf<R, ND, 4, S>::launch(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
+// stage 1, 2: Heun; 3, 4: van Leer predictor and corrector
+template <class R, class S = double>
+static cudaError_t launch_stage_prec(const StageArgs &a, int stage, cudaStream_t s) {
+    switch (a.g.ndim) {
+        case 1: return launch_stage_nd<R, 1, S>(a, stage, s);
+        case 2: return launch_stage_nd<R, 2, S>(a, stage, s);
+        case 3: return launch_stage_nd<R, 3, S>(a, stage, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class R, int ND, class S>
+static cudaError_t prepare_nd() {
+    cudaError_t e;
+    if ((e = StageOf<R, ND, 1, S>::prepare()) != cudaSuccess) return e;
+    if ((e = StageOf<R, ND, 2, S>::prepare()) != cudaSuccess) return e;
+    if ((e = StageOf<R, ND, 3, S>::prepare()) != cudaSuccess) return e;
+    return StageOf<R, ND, 4, S>::prepare();
+}
+
 template <class R, class S = double>
 static cudaError_t prepare_prec(int ndim) {
-    cudaError_t e;
     switch (ndim) {
-        case 1:
-            if ((e = StageOf<R, 1, 1, S>::prepare()) != cudaSuccess) return e;
-            return StageOf<R, 1, 2, S>::prepare();
-        case 2:
-            if ((e = StageOf<R, 2, 1, S>::prepare()) != cudaSuccess) return e;
-            return StageOf<R, 2, 2, S>::prepare();
-        case 3:
-            if ((e = StageOf<R, 3, 1, S>::prepare()) != cudaSuccess) return e;
-            return StageOf<R, 3, 2, S>::prepare();
+        case 1: return prepare_nd<R, 1, S>();
+        case 2: return prepare_nd<R, 2, S>();
+        case 3: return prepare_nd<R, 3, S>();
         default: return cudaErrorInvalidValue;
     }
 }

@@ -68,6 +68,8 @@ extern "C" khy_status khy_step_noalloc(const khy_mesh_desc *desc, double *U_dev,
     if (!U_dev || !out_dev) return (khy_status)record_error(KHY_ERR_ARG, "khy_step_noalloc: NULL state or output");
     if (desc->prec == KHY_PREC_FP32)
         return (khy_status)record_error(KHY_ERR_ARG, "khy_step_noalloc: FP64 or mixed precision only");
+    if (desc->integrator != KHY_INT_HEUN)
+        return (khy_status)record_error(KHY_ERR_ARG, "khy_step_noalloc: Heun integrator only");
     if (!(t == t) || !(t_end == t_end)) return (khy_status)record_error(KHY_ERR_ARG, "khy_step_noalloc: t or t_end is NaN");
     const Geom g = geom_of_desc(*desc);
     const size_t need = sizeof(double) * (size_t)(2 + desc->ndim) * (size_t)g.ncell;

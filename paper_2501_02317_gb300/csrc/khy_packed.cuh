@@ -121,15 +121,21 @@ __device__ __forceinline__ int rot_slot(int dir, int j) {
 }
 
 // Two face fluxes (lanes) from two four-cell stencils already rotated onto
-// their face normals: packed minmod PLM, then packed HLLC.  Fr is in rotated
+// their face normals: packed minmod PLM (or, PLM = false, the first-order
+// states of the van Leer predictor), then packed HLLC.  Fr is in rotated
 // order (mass, normal momentum, transverse momenta, energy).
-template <int ND>
+template <int ND, bool PLM = true>
 __device__ __forceinline__ void face_flux2(const float2 (&st)[4][ND + 2], const Consts<float> &k, float2 (&Fr)[ND + 2]) {
     constexpr int NT = ND - 1;
     float2 wl[NT + 3], wr[NT + 3];
     const float2 half = splat(0.5f), mhalf = splat(-0.5f);
 #pragma unroll
     for (int j = 0; j < ND + 2; ++j) {
+        if (!PLM) {
+            wl[j] = st[1][j];
+            wr[j] = st[2][j];
+            continue;
+        }
         const float2 d12 = sub2(st[2][j], st[1][j]);
         wl[j] = fma2(minmod2(sub2(st[1][j], st[0][j]), d12), half, st[1][j]);
         wr[j] = fma2(minmod2(d12, sub2(st[3][j], st[2][j])), mhalf, st[2][j]);

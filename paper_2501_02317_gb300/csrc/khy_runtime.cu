@@ -1,7 +1,9 @@
 // khy_runtime.cu -- host runtime behind the C ABI of include/khydro.h.
 //
-// A khy_sim owns U^n, U^1 (FP64, field-major) and a device Clock.  Steps are
-// recorded once into a CUDA graph of kStepsPerGraph Heun steps and replayed;
+// A khy_sim owns U^n and U^1 (FP64, field-major; with the van Leer
+// integrator the second array holds the half-step primitives W^{n+1/2} in the
+// flux precision instead) and a device Clock.  Steps are recorded once into a
+// CUDA graph of kStepsPerGraph steps and replayed;
 // the time step, the clip to t_end and the stop condition live on the device
 // (clock_kernel), so the host only polls the clock between graph replays.
 //
@@ -59,7 +61,8 @@ __global__ void clock_target_kernel(Clock *c, double t_end, long long max_steps)
 
 __global__ void clock_wmin_reset_kernel(Clock *c) { c->wmin_bits = kInfBits; }
 
-// primitive -> conserved (Eq. 2): m_d = rho v_d, E = p/(gamma-1) + (0.5 rho) |v|^2
+// primitive -> conserved (Eq. 2): m_d = rho v_d, E = p/(gamma-1) + (0.5 rho) |v|^2.
+// W may alias U: every cell's fields are read before they are written.
 template <int ND>
 __global__ void prim_to_cons_kernel(Geom g, const double *W, double *U) {
     constexpr int NV = ND + 2;
@@ -138,8 +141,9 @@ struct khy_sim {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    double *U = nullptr;   // U^n
-    double *U1 = nullptr;  // U^1; also scratch for khy_set_primitive
+    double *U = nullptr;   // U^n (FP32 values in the first half for KHY_PREC_FP32)
+    double *U1 = nullptr;  // U^1, or W^{n+1/2} (van Leer); also scratch of >= ncell doubles
+    size_t u_bytes = 0, u1_bytes = 0;
     Clock *clk = nullptr;
     Clock *clk_host = nullptr;  // pinned mirror for polling
     double *red = nullptr;      // totals partials [2*kTotalsBlocks]
@@ -173,6 +177,8 @@ khy_status validate(const khy_mesh_desc *d) {
     if (!(d->cfl > 0.0 && d->cfl <= 1.0)) return fail(KHY_ERR_ARG, "cfl must be in (0, 1]");
     if (d->prec != KHY_PREC_FP64 && d->prec != KHY_PREC_MIXED && d->prec != KHY_PREC_FP32)
         return fail(KHY_ERR_ARG, "prec must be a khy_prec");
+    if (d->integrator != KHY_INT_HEUN && d->integrator != KHY_INT_VL2)
+        return fail(KHY_ERR_ARG, "integrator must be a khy_integrator");
     if (!(d->rho_floor >= 0.0) || !(d->p_floor >= 0.0)) return fail(KHY_ERR_ARG, "floors must be >= 0");
     return KHY_OK;
 }
@@ -207,14 +213,17 @@ Geom make_geom(const khy_mesh_desc &d) {
     return g;
 }
 
-cudaError_t launch_stage(const khy_sim *s, int stage) {
+// Launches sub-step 1 or 2 of the simulation's integrator: Heun stages 1, 2
+// or van Leer stages 3 (predictor: U -> W^{n+1/2} in U1) and 4 (corrector:
+// W^{n+1/2}, U -> U).
+cudaError_t launch_stage(const khy_sim *s, int sub) {
     StageArgs a;
     a.g = s->geom;
     a.clk = s->clk;
     a.cubic = 1;
     for (int d = 1; d < s->geom.ndim; ++d)
         if (s->geom.dx[d] != s->geom.dx[0]) a.cubic = 0;
-    if (stage == 1) {
+    if (sub == 1) {
         a.Uin = s->U;
         a.Ubase = s->U;
         a.Uout = s->U1;
@@ -223,6 +232,7 @@ cudaError_t launch_stage(const khy_sim *s, int stage) {
         a.Ubase = s->U;
         a.Uout = s->U;
     }
+    const int stage = s->desc.integrator == KHY_INT_VL2 ? sub + 2 : sub;
     if (s->desc.prec == KHY_PREC_FP32) return launch_stage_single(a, stage, s->stream);
     return s->desc.prec == KHY_PREC_FP64 ? launch_stage_fp64(a, stage, s->stream)
                                          : launch_stage_mixed(a, stage, s->stream);
@@ -236,6 +246,30 @@ cudaError_t prepare_prec_of(const khy_sim *s) {
 bool single_state(const khy_sim *s) { return s->desc.prec == KHY_PREC_FP32; }
 
 int conv_blocks(long long n) { return (int)std::min<long long>((n + 255) / 256, 152 * 8); }
+
+// FP32 state <-> FP64 values, one field at a time through U1 (>= ncell
+// doubles in every configuration).  kind: the cudaMemcpyKind of src.
+cudaError_t fields_to_float(khy_sim *s, const double *src, cudaMemcpyKind kind) {
+    const long long N = s->geom.ncell;
+    float *Uf = reinterpret_cast<float *>(s->U);
+    for (int q = 0; q < 2 + s->desc.ndim; ++q) {
+        // float field q occupies bytes [4qN, 4(q+1)N) of U: for src == U those
+        // belong to FP64 fields < q (already converted) or to field 0 itself
+        cudaError_t e = cudaMemcpyAsync(s->U1, src + (long long)q * N, N * sizeof(double), kind, s->stream);
+        if (e != cudaSuccess) return e;
+        to_float_kernel<<<conv_blocks(N), 256, 0, s->stream>>>(s->U1, Uf + (long long)q * N, N);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// FP64 copy of field q of an FP32 state in U1
+cudaError_t field_to_double(khy_sim *s, int q) {
+    const long long N = s->geom.ncell;
+    to_double_kernel<<<conv_blocks(N), 256, 0, s->stream>>>(reinterpret_cast<const float *>(s->U) + (long long)q * N,
+                                                            s->U1, N);
+    return cudaGetLastError();
+}
 
 cudaError_t enqueue_one_step(const khy_sim *s) {
     clock_step_kernel<<<1, 1, 0, s->stream>>>(s->clk, s->geom);
@@ -330,8 +364,12 @@ khy_status khy_create(const khy_mesh_desc *desc, void *cuda_stream, khy_sim **ou
         }
     }
     const size_t bytes = sizeof(double) * (size_t)nvar_of(*desc) * (size_t)s->geom.ncell;
+    s->u_bytes = bytes;
+    // van Leer: the primitives W^{n+1/2} in the flux precision (FP32 in the
+    // mixed and FP32 paths); >= ncell doubles, which the FP32 conversions need
+    s->u1_bytes = (desc->integrator == KHY_INT_VL2 && desc->prec != KHY_PREC_FP64) ? bytes / 2 : bytes;
     if (e == cudaSuccess) e = cudaMalloc(&s->U, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&s->U1, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&s->U1, s->u1_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&s->clk, sizeof(Clock));
     if (e == cudaSuccess) e = cudaMalloc(&s->red, sizeof(double) * 2 * kTotalsBlocks);
     if (e == cudaSuccess) e = cudaMallocHost(&s->clk_host, sizeof(Clock));
@@ -385,10 +423,7 @@ khy_status khy_set_conserved_dev(khy_sim *s, const double *U_dev, size_t count) 
     khy_status st = check_count(s, count);
     if (st != KHY_OK) return st;
     if (single_state(s)) {
-        KHY_CUDA(cudaMemcpyAsync(s->U1, U_dev, count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
-        to_float_kernel<<<conv_blocks((long long)count), 256, 0, s->stream>>>(s->U1, reinterpret_cast<float *>(s->U),
-                                                                           (long long)count);
-        KHY_CUDA(cudaGetLastError());
+        KHY_CUDA(fields_to_float(s, U_dev, cudaMemcpyDeviceToDevice));
     } else {
         KHY_CUDA(cudaMemcpyAsync(s->U, U_dev, count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
     }
@@ -401,10 +436,7 @@ khy_status khy_set_conserved(khy_sim *s, const double *U, size_t count) {
     khy_status st = check_count(s, count);
     if (st != KHY_OK) return st;
     if (single_state(s)) {
-        KHY_CUDA(cudaMemcpyAsync(s->U1, U, count * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-        to_float_kernel<<<conv_blocks((long long)count), 256, 0, s->stream>>>(s->U1, reinterpret_cast<float *>(s->U),
-                                                                           (long long)count);
-        KHY_CUDA(cudaGetLastError());
+        KHY_CUDA(fields_to_float(s, U, cudaMemcpyHostToDevice));
     } else {
         KHY_CUDA(cudaMemcpyAsync(s->U, U, count * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     }
@@ -413,20 +445,16 @@ khy_status khy_set_conserved(khy_sim *s, const double *U, size_t count) {
     return KHY_OK;
 }
 
+// primitive values already copied into U (FP64) -> conserved, in place
 static khy_status convert_prim(khy_sim *s) {
     const int blocks = (int)std::min<long long>((s->geom.ncell + 255) / 256, 152 * 8);
     switch (s->desc.ndim) {
-        case 1: prim_to_cons_kernel<1><<<blocks, 256, 0, s->stream>>>(s->geom, s->U1, s->U); break;
-        case 2: prim_to_cons_kernel<2><<<blocks, 256, 0, s->stream>>>(s->geom, s->U1, s->U); break;
-        default: prim_to_cons_kernel<3><<<blocks, 256, 0, s->stream>>>(s->geom, s->U1, s->U); break;
+        case 1: prim_to_cons_kernel<1><<<blocks, 256, 0, s->stream>>>(s->geom, s->U, s->U); break;
+        case 2: prim_to_cons_kernel<2><<<blocks, 256, 0, s->stream>>>(s->geom, s->U, s->U); break;
+        default: prim_to_cons_kernel<3><<<blocks, 256, 0, s->stream>>>(s->geom, s->U, s->U); break;
     }
     KHY_CUDA(cudaGetLastError());
-    if (single_state(s)) {  // FP64 conserved values in U -> FP32 state (staged through U1)
-        const long long n = (long long)nvar_of(s->desc) * s->geom.ncell;
-        to_float_kernel<<<conv_blocks(n), 256, 0, s->stream>>>(s->U, reinterpret_cast<float *>(s->U1), n);
-        KHY_CUDA(cudaGetLastError());
-        KHY_CUDA(cudaMemcpyAsync(s->U, s->U1, n * sizeof(float), cudaMemcpyDeviceToDevice, s->stream));
-    }
+    if (single_state(s)) KHY_CUDA(fields_to_float(s, s->U, cudaMemcpyDeviceToDevice));
     s->wmin_valid = false;
     return KHY_OK;
 }
@@ -435,7 +463,7 @@ khy_status khy_set_primitive(khy_sim *s, const double *W, size_t count) {
     if (!s || !W) return fail(KHY_ERR_ARG, "NULL argument");
     khy_status st = check_count(s, count);
     if (st != KHY_OK) return st;
-    KHY_CUDA(cudaMemcpyAsync(s->U1, W, count * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    KHY_CUDA(cudaMemcpyAsync(s->U, W, count * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     st = convert_prim(s);
     if (st != KHY_OK) return st;
     KHY_CUDA(cudaStreamSynchronize(s->stream));
@@ -446,7 +474,7 @@ khy_status khy_set_primitive_dev(khy_sim *s, const double *W_dev, size_t count) 
     if (!s || !W_dev) return fail(KHY_ERR_ARG, "NULL argument");
     khy_status st = check_count(s, count);
     if (st != KHY_OK) return st;
-    KHY_CUDA(cudaMemcpyAsync(s->U1, W_dev, count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    KHY_CUDA(cudaMemcpyAsync(s->U, W_dev, count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
     return convert_prim(s);
 }
 
@@ -549,10 +577,12 @@ khy_status khy_get_conserved(khy_sim *s, double *U, size_t count) {
     khy_status st = check_count(s, count);
     if (st != KHY_OK) return st;
     if (single_state(s)) {
-        to_double_kernel<<<conv_blocks((long long)count), 256, 0, s->stream>>>(reinterpret_cast<const float *>(s->U),
-                                                                            s->U1, (long long)count);
-        KHY_CUDA(cudaGetLastError());
-        KHY_CUDA(cudaMemcpyAsync(U, s->U1, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        const long long N = s->geom.ncell;
+        for (int q = 0; q < nvar_of(s->desc); ++q) {
+            KHY_CUDA(field_to_double(s, q));
+            KHY_CUDA(cudaMemcpyAsync(U + (long long)q * N, s->U1, N * sizeof(double), cudaMemcpyDeviceToHost,
+                                     s->stream));
+        }
     } else {
         KHY_CUDA(cudaMemcpyAsync(U, s->U, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     }
@@ -565,9 +595,12 @@ khy_status khy_get_conserved_dev(khy_sim *s, double *U_dev, size_t count) {
     khy_status st = check_count(s, count);
     if (st != KHY_OK) return st;
     if (single_state(s)) {
-        to_double_kernel<<<conv_blocks((long long)count), 256, 0, s->stream>>>(reinterpret_cast<const float *>(s->U),
-                                                                            U_dev, (long long)count);
-        KHY_CUDA(cudaGetLastError());
+        const long long N = s->geom.ncell;
+        for (int q = 0; q < nvar_of(s->desc); ++q) {
+            KHY_CUDA(field_to_double(s, q));
+            KHY_CUDA(cudaMemcpyAsync(U_dev + (long long)q * N, s->U1, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     s->stream));
+        }
     } else {
         KHY_CUDA(cudaMemcpyAsync(U_dev, s->U, count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
     }
@@ -589,15 +622,13 @@ khy_status khy_totals(khy_sim *s, double out[5]) {
     const int nv = nvar_of(s->desc);
     const long long N = s->geom.ncell;
     const int blocks = (int)std::min<long long>((N + 255) / 256, kTotalsBlocks);
-    const double *src = s->U;
-    if (single_state(s)) {
-        to_double_kernel<<<conv_blocks((long long)nv * N), 256, 0, s->stream>>>(reinterpret_cast<const float *>(s->U),
-                                                                             s->U1, (long long)nv * N);
-        KHY_CUDA(cudaGetLastError());
-        src = s->U1;
-    }
     for (int q = 0; q < nv; ++q) {
-        totals_kernel<<<blocks, 256, 0, s->stream>>>(src + (long long)q * N, N, s->red);
+        const double *src = s->U + (long long)q * N;
+        if (single_state(s)) {
+            KHY_CUDA(field_to_double(s, q));
+            src = s->U1;
+        }
+        totals_kernel<<<blocks, 256, 0, s->stream>>>(src, N, s->red);
         KHY_CUDA(cudaGetLastError());
         KHY_CUDA(cudaMemcpyAsync(s->red_host, s->red, sizeof(double) * 2 * blocks, cudaMemcpyDeviceToHost, s->stream));
         KHY_CUDA(cudaStreamSynchronize(s->stream));
@@ -632,6 +663,13 @@ khy_status khy_get_flags(khy_sim *s, unsigned *flags, unsigned long long *floor_
                                  cudaMemcpyHostToDevice, s->stream));
         KHY_CUDA(cudaStreamSynchronize(s->stream));
     }
+    return KHY_OK;
+}
+
+khy_status khy_device_bytes(khy_sim *s, size_t *state_bytes, size_t *total_bytes) {
+    if (!s) return fail(KHY_ERR_ARG, "sim is NULL");
+    if (state_bytes) *state_bytes = s->u_bytes + s->u1_bytes;
+    if (total_bytes) *total_bytes = s->u_bytes + s->u1_bytes + sizeof(Clock) + sizeof(double) * 2 * kTotalsBlocks;
     return KHY_OK;
 }
 

@@ -473,8 +473,8 @@ khy_status khy_server_submit(khy_server *s, const khy_mesh_desc *desc, const dou
     if (!s || !desc || !W || !job_id) return sfail(KHY_ERR_ARG, "khy_server_submit: NULL argument");
     int st = validate_desc(desc);
     if (st != KHY_OK) return (khy_status)st;
-    if (desc->ndim < 2 || desc->prec != KHY_PREC_MIXED)
-        return sfail(KHY_ERR_ARG, "khy_server_submit: the server runs mixed-precision 2D and 3D jobs");
+    if (desc->ndim < 2 || desc->prec != KHY_PREC_MIXED || desc->integrator != KHY_INT_HEUN)
+        return sfail(KHY_ERR_ARG, "khy_server_submit: the server runs mixed-precision 2D and 3D Heun jobs");
     if (!(t_end > 0.0) || !std::isfinite(t_end)) return sfail(KHY_ERR_ARG, "khy_server_submit: t_end must be > 0");
     Job j;
     j.desc = *desc;

@@ -9,6 +9,14 @@
 //   stage_kernel 2 : Un+1 = (Un + (U1 + dt L(U1))) / 2 written over Un, plus the
 //                    CFL minimum of Un+1 for the next step (Sec. 3.1: the step
 //                    length comes out of the variable conversion).
+// The memory-optimized van Leer integrator (Sec. 3.3) replaces the two stage
+// launches with
+//   stage_kernel 3 : predictor, U^{n+1/2} = Un + (dt/2) L_1(Un) with
+//                    first-order face states; only its primitives W^{n+1/2}
+//                    are stored (in the flux precision R: FP32 in the mixed
+//                    path), in place of U1
+//   stage_kernel 4 : corrector, Un+1 = Un + dt L(W^{n+1/2}) with PLM face
+//                    states of W^{n+1/2}, written over Un, plus the CFL minimum.
 //
 // Work decomposition.  The grid is cut into tiles of TX x TY columns along
 // the slowest ("march") axis -- z in 3D, y in 2D; a 1D grid is one row.  The
@@ -44,9 +52,9 @@ namespace khy {
 
 struct StageArgs {
     Geom g;
-    const double *Uin;    // state the fluxes are computed from (Un or U1)
-    const double *Ubase;  // Un (stage 2 average); unused in stage 1
-    double *Uout;         // U1 (stage 1) or Un+1 (stage 2, may alias Ubase)
+    const double *Uin;    // state the fluxes are computed from (Un, U1; stage 4: W^{n+1/2})
+    const double *Ubase;  // Un (stages 2 and 4); unused in stages 1 and 3
+    double *Uout;         // U1 (stage 1), W^{n+1/2} (stage 3) or Un+1 (stages 2, 4; may alias Ubase)
     Clock *clk;
     int cubic;            // mixed path: all active dx equal (one dt/dx factor)
 };
@@ -84,6 +92,11 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     constexpr bool MIX = std::is_same<R, float>::value;
     constexpr bool SINGLE = std::is_same<S, float>::value;
     static_assert(!SINGLE || MIX, "an FP32 state needs FP32 fluxes");
+    static_assert(STAGE >= 1 && STAGE <= 4, "stages 1, 2 (Heun) and 3, 4 (van Leer)");
+    constexpr bool PLM = STAGE != 3;                  // the predictor uses first-order face states
+    constexpr bool CFL = STAGE == 2 || STAGE == 4;    // last stage of a step: CFL minimum of Un+1
+    constexpr bool FROM_W = STAGE == 4;               // fluxes from stored primitives (type R)
+    constexpr bool TO_W = STAGE == 3;                 // writes primitives (type R) instead of a state
     using T = Tile<ND, TX, TY>;
     constexpr int NV = T::NV, PX = T::PX, PC = T::PC, NT = T::NT;
     constexpr int DM = ND - 1;  // march axis (ND >= 2)
@@ -97,10 +110,15 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     const int wact = min(TX, g.n[0] - x0);
     const int hact = (ND == 3) ? min(TY, g.n[1] - y0) : 1;
 
+    // the step's dt/dx, halved for the van Leer predictor (a power-of-two
+    // scaling: the same bits as (dt/2)/dx)
+    double dtq[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dtq[d] = STAGE == 3 ? 0.5 * dtdx[d] : dtdx[d];
     // dt/dx and dt/(2 dx) rounded to FP32 once (they scale the small
     // low-order part of the flux sums in the mixed update)
-    const float c32 = mx::d2f(dtdx[0]), hc32 = mx::d2f(0.5 * dtdx[0]);
-    const float c32x = c32, c32y = mx::d2f(dtdx[1]), c32m = mx::d2f(dtdx[DM < 0 ? 0 : DM]);
+    const float c32 = mx::d2f(dtq[0]), hc32 = mx::d2f(0.5 * dtq[0]);
+    const float c32x = c32, c32y = mx::d2f(dtq[1]), c32m = mx::d2f(dtq[DM < 0 ? 0 : DM]);
 
     // tiles whose halo box lies inside the grid skip the ghost-zone index map
     const bool x_inside = x0 >= 2 && x0 + wact + 2 <= g.n[0];
@@ -130,7 +148,11 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
             const long long idx = ((long long)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
             R w[NV];
             unsigned fl = 0;
-            if constexpr (SINGLE) {
+            if constexpr (FROM_W) {  // stored primitives: no recovery
+                const R *Wsrc = reinterpret_cast<const R *>(Uin);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) w[q] = __ldg(Wsrc + (long long)q * N + idx);
+            } else if constexpr (SINGLE) {
                 float u[NV];
 #pragma unroll
                 for (int q = 0; q < NV; ++q) u[q] = __ldg(Uin + (long long)q * N + idx);
@@ -178,7 +200,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 if (fx > wact || fy >= hact) continue;
                 const int hy = (ND == 3) ? fy + 2 : 0;
                 gather(pl, hy * PX + fx, 1, s);
-                face_flux<ND, R>(s, 0, kc, F);
+                face_flux<ND, R, PLM>(s, 0, kc, F);
 #pragma unroll
                 for (int q = 0; q < NV; ++q) sFx[(size_t)q * T::NXF + f] = F[q];
             } else {
@@ -186,7 +208,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 const int fxx = f2 % TX, fyy = f2 / TX;
                 if (fxx >= wact || fyy > hact) continue;
                 gather(pl, fyy * PX + fxx + 2, PX, s);
-                face_flux<ND, R>(s, 1, kc, F);
+                face_flux<ND, R, PLM>(s, 1, kc, F);
 #pragma unroll
                 for (int q = 0; q < NV; ++q) sFy[(size_t)q * T::NYF + f2] = F[q];
             }
@@ -265,7 +287,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                                            pb[(size_t)pk::rot_slot<ND>(tb.dir, j) * PC]);
             }
             float2 Fr[NV];
-            pk::face_flux2<ND>(st, kc_f, Fr);
+            pk::face_flux2<ND, PLM>(st, kc_f, Fr);
             if (va) {
 #pragma unroll
                 for (int j = 0; j < NV; ++j) ta.dst[(size_t)pk::rot_slot<ND>(ta.dir, j) * ta.dstride] = Fr[j].x;
@@ -277,13 +299,17 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
         }
     };
 
-    // conservative update of cell (tx, ty) of plane cur (Sec. 3.3)
+    // conservative update of cell (tx, ty) of plane cur (Sec. 3.3): stages 1,
+    // 3 and 4 add dt L (or dt/2 L) to Un, stage 2 takes the Heun average.
+    // The stage-3 result is only recovered to primitives and stored.
     auto update_cell = [&](int cur, const R (&Fmlo)[NV], const R (&Fmhi)[NV]) {
         const int gx = x0 + tx;
         const int gy = (ND == 3) ? y0 + ty : (ND == 2 ? cur : 0);
         const int gz = (ND == 3) ? cur : 0;
         if (gx >= g.n[0] || (ND == 3 && gy >= g.n[1])) return;
         const long long idx = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
+        const S *Ucell = FROM_W ? Ubase : Uin;  // the state this stage adds to
+        R *Wout = reinterpret_cast<R *>(Uout);
         if constexpr (SINGLE) {  // all-FP32: U + dt L(U) in FP32, directions in x, y, z order
             float un[NV];
 #pragma unroll
@@ -293,14 +319,20 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 float acc = __fmul_rn(c32x, __fsub_rn(fx[0], fx[1]));
                 if (ND == 3) acc = __fmaf_rn(c32y, __fsub_rn(fy[0], fy[TX]), acc);
                 if (ND >= 2) acc = __fmaf_rn(c32m, __fsub_rn((float)Fmlo[q], (float)Fmhi[q]), acc);
-                const float u = Uin[(long long)q * N + idx];
+                const float u = Ucell[(long long)q * N + idx];
                 float r;
-                if (STAGE == 1) r = __fadd_rn(u, acc);
+                if (STAGE != 2) r = __fadd_rn(u, acc);
                 else r = __fmul_rn(0.5f, __fadd_rn(Ubase[(long long)q * N + idx], __fadd_rn(u, acc)));
                 un[q] = r;
-                Uout[(long long)q * N + idx] = r;
+                if (!TO_W) Uout[(long long)q * N + idx] = r;
             }
-            if (STAGE == 2) {
+            if (TO_W) {
+                float w[NV];
+                sg::recover<ND>(un, mk, w, flags, floors);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) Wout[(long long)q * N + idx] = w[q];
+            }
+            if (CFL) {
                 const double c = (double)sg::cfl_candidate<ND>(un, mk);
                 wmin = c < wmin ? c : wmin;
             }
@@ -310,14 +342,14 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
         for (int q = 0; q < NV; ++q) {
             const R *fx = sFx + (size_t)q * T::NXF + ty * (TX + 1) + tx;
             const R *fy = sFy + (size_t)q * T::NYF + ty * TX + tx;
-            const double u = (double)Uin[(long long)q * N + idx];
+            const double u = (double)Ucell[(long long)q * N + idx];
             double r;
             if constexpr (!MIX) {
                 // dU = -sum_d (dt/dx_d)(F_hi - F_lo), directions in x, y, z order
-                double acc = 0.0 - dtdx[0] * (fx[1] - fx[0]);
-                if (ND == 3) acc = acc - dtdx[1] * (fy[TX] - fy[0]);
-                if (ND >= 2) acc = acc - dtdx[DM] * (Fmhi[q] - Fmlo[q]);
-                if (STAGE == 1) r = u + acc;
+                double acc = 0.0 - dtq[0] * (fx[1] - fx[0]);
+                if (ND == 3) acc = acc - dtq[1] * (fy[TX] - fy[0]);
+                if (ND >= 2) acc = acc - dtq[DM] * (Fmhi[q] - Fmlo[q]);
+                if (STAGE != 2) r = u + acc;
                 else r = 0.5 * (Ubase[(long long)q * N + idx] + (u + acc));
             } else {
                 // F_lo - F_hi per direction, exact as float-float pairs
@@ -326,31 +358,38 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 if (ND == 3) Dy = mx::two_sum(fy[0], -fy[TX]);
                 if (ND >= 2) Dm = mx::two_sum(Fmlo[q], -Fmhi[q]);
                 if (cubic) {
-                    mx::FF S = Dx;
-                    if (ND == 3) S = mx::ff_add(S, Dy);
-                    if (ND >= 2) S = mx::ff_add(S, Dm);
-                    const double c = dtdx[0];
-                    if (STAGE == 1) {
-                        const double lo = mx::f2d(__fmul_rn(c32, S.lo));
-                        r = __fma_rn(c, mx::f2d(S.hi), __dadd_rn(u, lo));
+                    mx::FF Fs = Dx;
+                    if (ND == 3) Fs = mx::ff_add(Fs, Dy);
+                    if (ND >= 2) Fs = mx::ff_add(Fs, Dm);
+                    const double c = dtq[0];
+                    if (STAGE != 2) {
+                        const double lo = mx::f2d(__fmul_rn(c32, Fs.lo));
+                        r = __fma_rn(c, mx::f2d(Fs.hi), __dadd_rn(u, lo));
                     } else {
                         const double hc = 0.5 * c;
-                        const double lo = mx::f2d(__fmul_rn(hc32, S.lo));
+                        const double lo = mx::f2d(__fmul_rn(hc32, Fs.lo));
                         const double A = __dadd_rn(Ubase[(long long)q * N + idx], u);
-                        r = __fma_rn(hc, mx::f2d(S.hi), __fma_rn(0.5, A, lo));
+                        r = __fma_rn(hc, mx::f2d(Fs.hi), __fma_rn(0.5, A, lo));
                     }
                 } else {
-                    double acc = __fma_rn(dtdx[0], mx::f2d(Dx.hi), __dmul_rn(dtdx[0], mx::f2d(Dx.lo)));
-                    if (ND == 3) acc = __fma_rn(dtdx[1], mx::f2d(Dy.hi), __fma_rn(dtdx[1], mx::f2d(Dy.lo), acc));
-                    if (ND >= 2) acc = __fma_rn(dtdx[DM], mx::f2d(Dm.hi), __fma_rn(dtdx[DM], mx::f2d(Dm.lo), acc));
-                    if (STAGE == 1) r = __dadd_rn(u, acc);
+                    double acc = __fma_rn(dtq[0], mx::f2d(Dx.hi), __dmul_rn(dtq[0], mx::f2d(Dx.lo)));
+                    if (ND == 3) acc = __fma_rn(dtq[1], mx::f2d(Dy.hi), __fma_rn(dtq[1], mx::f2d(Dy.lo), acc));
+                    if (ND >= 2) acc = __fma_rn(dtq[DM], mx::f2d(Dm.hi), __fma_rn(dtq[DM], mx::f2d(Dm.lo), acc));
+                    if (STAGE != 2) r = __dadd_rn(u, acc);
                     else r = __dmul_rn(0.5, __dadd_rn(Ubase[(long long)q * N + idx], __dadd_rn(u, acc)));
                 }
             }
             un[q] = r;
-            Uout[(long long)q * N + idx] = r;
+            if (!TO_W) Uout[(long long)q * N + idx] = r;
         }
-        if (STAGE == 2) {  // CFL candidate of the new state for the next step
+        if (TO_W) {  // primitives of U^{n+1/2}, floors counted like any recovery
+            R w[NV];
+            if constexpr (MIX) mx::recover<ND>(un, mk, w, flags, floors);
+            else recover<ND>(un, g, w, flags, floors);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) Wout[(long long)q * N + idx] = w[q];
+        }
+        if (CFL) {  // CFL candidate of the new state for the next step
             double c;
             if constexpr (MIX) {
                 c = mx::f2d(mx::cfl_candidate<ND>(un, mk));
@@ -413,7 +452,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
 #pragma unroll
                         for (int q = 0; q < NV; ++q) s[o][q] = pl[(size_t)q * PC + e];
                     }
-                    face_flux<ND, R>(s, DM, kc, Fmhi);
+                    face_flux<ND, R, PLM>(s, DM, kc, Fmhi);
                 }
                 if (cur >= k0) inplane_faces(cur & 3);
                 __syncthreads();
@@ -455,7 +494,7 @@ __device__ __forceinline__ void reduce_to_clock(Clock *clk, unsigned flags, unsi
     if (tid == 0) {
         if (s_flags) atomicOr(&clk->status, s_flags);
         if (s_floors) atomicAdd(&clk->floor_hits, s_floors);
-        if (STAGE == 2) {
+        if (STAGE == 2 || STAGE == 4) {
             double m = s_wmin[0];
             for (int i = 1; i < NT / 32; ++i) m = s_wmin[i] < m ? s_wmin[i] : m;
             if (m < __longlong_as_double((long long)kInfBits))

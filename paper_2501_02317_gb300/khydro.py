@@ -33,6 +33,7 @@ EXPORTS = [
     "khy_set_conserved_dev", "khy_set_primitive_dev", "khy_set_time", "khy_step_to",
     "khy_enqueue_steps", "khy_get_conserved", "khy_get_conserved_dev", "khy_get_time", "khy_totals",
     "khy_get_flags", "khy_last_error", "khy_version", "khy_profile_steps", "khy_step_noalloc",
+    "khy_device_bytes",
     "khy_batch_create", "khy_batch_destroy", "khy_batch_set_primitive", "khy_batch_set_conserved",
     "khy_batch_get_conserved", "khy_batch_set_target", "khy_batch_enqueue_steps", "khy_batch_run",
     "khy_batch_get_clock", "khy_batch_autotune", "khy_batch_set_variant", "khy_batch_profile_steps",
@@ -57,6 +58,7 @@ class khy_mesh_desc(ctypes.Structure):
         ("cfl", ctypes.c_double),
         ("prec", ctypes.c_int),
         ("bc", (ctypes.c_int * 2) * 3),
+        ("integrator", ctypes.c_int),
         ("rho_floor", ctypes.c_double),
         ("p_floor", ctypes.c_double),
     ]
@@ -74,6 +76,7 @@ def desc_of(mesh: Mesh) -> khy_mesh_desc:
     d.gamma = float(mesh.gamma)
     d.cfl = float(mesh.cfl)
     d.prec = int(mesh.prec)
+    d.integrator = int(getattr(mesh, "integrator", 0))
     d.rho_floor = float(mesh.rho_floor)
     d.p_floor = float(mesh.p_floor)
     return d
@@ -109,6 +112,7 @@ def lib() -> ctypes.CDLL:
         "khy_totals": [vp, vp],
         "khy_get_flags": [vp, P(ctypes.c_uint), P(ctypes.c_ulonglong), i],
         "khy_profile_steps": [vp, d, l, P(ctypes.c_float)],
+        "khy_device_bytes": [vp, P(st), P(st)],
         "khy_step_noalloc": [P(khy_mesh_desc), vp, d, d, vp, vp],
         "khy_batch_create": [P(khy_mesh_desc), i, vp, P(vp)],
         "khy_batch_set_primitive": [vp, vp, st],
@@ -263,6 +267,14 @@ def khy_get_flags(h, clear: bool = False) -> Tuple[int, int]:
     return f.value, n.value
 
 
+def khy_device_bytes(h) -> Tuple[int, int]:
+    """(state bytes, total bytes) of device memory held by a simulation."""
+    a = ctypes.c_size_t()
+    b = ctypes.c_size_t()
+    _check(lib().khy_device_bytes(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 # ------------------------------------------------------------ wrapper
 
 class Sim:
@@ -324,6 +336,9 @@ class Sim:
 
     def flags(self, clear: bool = False) -> Tuple[int, int]:
         return khy_get_flags(self.h, clear)
+
+    def device_bytes(self) -> Tuple[int, int]:
+        return khy_device_bytes(self.h)
 
 
 # ------------------------------------------------------------ many grids

@@ -35,6 +35,10 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 PREC_FP32 = 2
 
+# time integrators (Sec. 3.3): Heun, memory-optimized van Leer
+INT_HEUN = 0
+INT_VL2 = 1
+
 DEFAULT_FLOOR = 1e-10
 
 
@@ -56,6 +60,7 @@ class Mesh:
     prec: int = PREC_FP64
     rho_floor: float = DEFAULT_FLOOR
     p_floor: float = DEFAULT_FLOOR
+    integrator: int = INT_HEUN
 
     @property
     def nvar(self) -> int:

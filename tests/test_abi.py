@@ -86,5 +86,6 @@ def test_desc_struct_layout_matches_header():
     d = khydro.khy_mesh_desc
     assert d.ndim.offset == 0 and d.n.offset == 4 and d.lo.offset == 16
     assert d.hi.offset == 40 and d.gamma.offset == 64 and d.cfl.offset == 72 and d.prec.offset == 80
-    assert d.bc.offset == 84 and d.rho_floor.offset == 112 and d.p_floor.offset == 120
+    assert d.bc.offset == 84 and d.integrator.offset == 108
+    assert d.rho_floor.offset == 112 and d.p_floor.offset == 120
     assert ctypes.sizeof(d) == 128

@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_vl2_pins as vpins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "khydro_oracle.c")
 
@@ -42,10 +43,19 @@ MUTANTS = {
     "two_shock_sign": ("pstar = (gl * pl + gr * pr - (ur - ul)) / (gl + gr);", "pstar = (gl * pl + gr * pr + (ur - ul)) / (gl + gr);"),
     "sound_speed_gamma": ("double cl = sqrt(gamma * pl / rl);", "double cl = sqrt(pl / rl);"),
     "prim_to_cons_energy": ("p / gm1 + 0.5 * rho * vsq", "p / gm1 + rho * vsq"),
+    # van Leer integrator (Sec. 3.3)
+    "vl2_predictor_full_dt": ("rhs_order(m, U, 0.5 * dt, 1, dU, flags);", "rhs_order(m, U, dt, 1, dU, flags);"),
+    "vl2_predictor_plm": ("rhs_order(m, U, 0.5 * dt, 1, dU, flags);", "rhs_order(m, U, 0.5 * dt, 2, dU, flags);"),
+    "vl2_corrector_first_order": ("rhs_order(m, Uh, dt, 2, dU, flags);", "rhs_order(m, Uh, dt, 1, dU, flags);"),
+    "vl2_corrector_from_old_state": ("rhs_order(m, Uh, dt, 2, dU, flags);", "rhs_order(m, U, dt, 2, dU, flags);"),
+    "vl2_corrector_base": ("for (long q = 0; q < NV; ++q) U[q] = U[q] + dU[q];",
+                           "for (long q = 0; q < NV; ++q) U[q] = Uh[q] + dU[q];"),
+    "first_order_downwind": ("wl[q] = s[1][q];", "wl[q] = s[2][q];"),
 }
 
 # fast pins first; each entry is a zero-argument callable
 PIN_CHECKS = [
+    lambda: [vpins.test_contact_advection_reduces_to_scalar_scheme(i, u) for i in (0, 1) for u in (0.5, -0.35)],
     lambda: [pins.test_minmod_truth_table(a, b, w) for a, b, w in
              [(1.0, 2.0, 1.0), (2.0, 1.0, 1.0), (-1.0, -3.0, -1.0), (1.0, -1.0, 0.0)]],
     pins.test_hllc_consistency,
@@ -66,6 +76,12 @@ PIN_CHECKS = [
     pins.test_axis_interchange_identical,
     lambda: [pins.test_axis_permutation_covariance(nd, pm) for nd, pm in
              [(2, (1, 0)), (3, (1, 2, 0)), (3, (0, 2, 1))]],
+    lambda: [vpins.test_vl2_uniform_state_stays_uniform(nd) for nd in (1, 2, 3)],
+    lambda: [vpins.test_vl2_conservation_periodic(nd) for nd in (1, 2, 3)],
+    vpins.test_vl2_sod_against_exact_solution,
+    vpins.test_vl2_sound_wave_second_order,
+    vpins.test_vl2_axis_interchange_identical,
+    vpins.test_vl2_implosion_diagonal_symmetry,
 ]
 
 
