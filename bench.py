@@ -356,6 +356,7 @@ def main():
 
     fp32 = leg(wl.PREC_FP32, wl.INT_HEUN, K, BYTES_PER_CELL_UPDATE_3D_FP32)
     vl2 = leg(wl.PREC_MIXED, wl.INT_VL2, K, BYTES_PER_CELL_UPDATE_3D_VL2)
+    lean = leg(wl.PREC_MIXED, wl.INT_HEUN_LEAN, K, BYTES_PER_CELL_UPDATE_3D)
 
     # ---------------------------------------------------------- end to end (host buffers)
     e2e = None
@@ -398,6 +399,7 @@ def main():
             "mixed_over_fp64": value / value64,
             "fp32": dict(fp32, workload="turbulence-3d-%d^3-fp32 (FP32 state and flux)" % args.n),
             "vl2_mixed": dict(vl2, workload="turbulence-3d-%d^3-mixed, memory-optimized van Leer integrator" % args.n),
+            "heun_lean_mixed": dict(lean, workload="turbulence-3d-%d^3-mixed, Heun without stored primitives" % args.n),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                          "frac": achieved / peak_gbs,
                          "traffic": _recorded_traffic("turbulence-3d-%d^3-mixed" % args.n),

@@ -69,6 +69,13 @@ typedef enum {
 
 /* Time integrator (Sec. 3.3).
  *   KHY_INT_HEUN: U^1 = U^n + dt L(U^n); U^{n+1} = (U^n + (U^1 + dt L(U^1))) / 2.
+ *                 A single grid also keeps the primitives of U^n and U^1 in
+ *                 device memory (flux precision), so the stage kernels read
+ *                 them instead of recovering every halo cell again: state
+ *                 memory 120 B per 3D cell in the mixed path (160 B FP64).
+ *   KHY_INT_HEUN_LEAN: the same Heun step, bit for bit, without the stored
+ *                 primitives (halo cells are recovered on the fly): 80 B per
+ *                 3D cell in the mixed path, slower.
  *   KHY_INT_VL2 : memory-optimized van Leer predictor-corrector: the
  *                 predictor U^{n+1/2} = U^n + (dt/2) L_1(U^n) uses first-order
  *                 (piecewise-constant) face states and only its primitives
@@ -78,7 +85,7 @@ typedef enum {
  *                 becomes a primitive array (FP32 in the mixed and FP32 paths),
  *                 and the result is U^n plus flux differences only, so it is
  *                 conservative to round-off.  Single grids only. */
-typedef enum { KHY_INT_HEUN = 0, KHY_INT_VL2 = 1 } khy_integrator;
+typedef enum { KHY_INT_HEUN = 0, KHY_INT_VL2 = 1, KHY_INT_HEUN_LEAN = 2 } khy_integrator;
 
 /* Mesh and method parameters.  n[d] >= 2 for d < ndim and n[d] == 1 for
  * d >= ndim; hi[d] > lo[d]; gamma > 1; 0 < cfl <= 1; floors >= 0.  A zeroed
@@ -102,8 +109,9 @@ typedef struct khy_sim khy_sim;
 /* ------------------------------------------------------------ single grid */
 
 /* Validates *desc, allocates the state (U^n, and U^1 or the van Leer
- * primitives W^{n+1/2}) and the device clock on the current CUDA device, and
- * binds the stream (cudaStream_t, may be NULL).
+ * primitives W^{n+1/2}; for KHY_INT_HEUN the primitives of U^n and U^1) and
+ * the device clock on the current CUDA device, and binds the stream
+ * (cudaStream_t, may be NULL).
  * On success *out receives the simulation, time t = 0, state zero.
  * Errors: KHY_ERR_ARG (invalid desc), KHY_ERR_OOM, KHY_ERR_CUDA. */
 khy_status khy_create(const khy_mesh_desc *desc, void *cuda_stream, khy_sim **out);
@@ -169,9 +177,10 @@ khy_status khy_totals(khy_sim *sim, double out[5]);
  * applied) and the number of floor applications; clears them when clear != 0. */
 khy_status khy_get_flags(khy_sim *sim, unsigned *flags, unsigned long long *floor_hits, int clear);
 
-/* Device memory held by the simulation, in bytes: *state_bytes for the two
- * state arrays (U^n and U^1, or U^n and W^{n+1/2}), *total_bytes including
- * the clock and reduction buffers.  Either pointer may be NULL. */
+/* Device memory held by the simulation, in bytes: *state_bytes for the state
+ * arrays (U^n and U^1 or W^{n+1/2}, and the stored primitives of KHY_INT_HEUN),
+ * *total_bytes including the clock and reduction buffers.  Either pointer may
+ * be NULL. */
 khy_status khy_device_bytes(khy_sim *sim, size_t *state_bytes, size_t *total_bytes);
 
 /* ------------------------------------------------------------ many grids */
@@ -187,7 +196,8 @@ khy_status khy_device_bytes(khy_sim *sim, size_t *state_bytes, size_t *total_byt
 typedef struct khy_batch khy_batch;
 
 /* Validates every descriptor (same ndim and prec for all; KHY_PREC_FP64 or
- * KHY_PREC_MIXED; KHY_INT_HEUN), allocates the pooled states and the clocks,
+ * KHY_PREC_MIXED; KHY_INT_HEUN or KHY_INT_HEUN_LEAN, both run as the lean
+ * Heun step), allocates the pooled states and the clocks,
  * binds the stream (NULL: a private stream)
  * and builds the segment schedule for the tile variant remembered for this
  * batch shape (variant 0 if none was tuned).  Targets start at t_end = 0, so
@@ -255,7 +265,7 @@ khy_status khy_server_create(size_t hbm_budget_bytes, int max_slots, void *cuda_
  * frees everything. */
 void khy_server_destroy(khy_server *s);
 
-/* Queues a job: mesh desc (ndim 2 or 3, KHY_PREC_MIXED, KHY_INT_HEUN), primitive initial
+/* Queues a job: mesh desc (ndim 2 or 3, KHY_PREC_MIXED, a Heun integrator), primitive initial
  * state W (host, count = nvar*ncell doubles, copied), target time t_end > 0.
  * *job_id receives the job's id.  KHY_ERR_BUDGET if the job's two states
  * cannot fit the arena even when it is empty. */

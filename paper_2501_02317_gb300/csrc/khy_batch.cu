@@ -348,7 +348,7 @@ khy_status khy_batch_create(const khy_mesh_desc *descs, int ngrids, void *cuda_s
         if (descs[i].ndim != descs[0].ndim || descs[i].prec != descs[0].prec)
             return bfail(KHY_ERR_ARG, "khy_batch_create: all grids must share ndim and prec");
         if (descs[i].prec == KHY_PREC_FP32) return bfail(KHY_ERR_ARG, "khy_batch_create: FP64 or mixed precision only");
-        if (descs[i].integrator != KHY_INT_HEUN) return bfail(KHY_ERR_ARG, "khy_batch_create: Heun integrator only");
+        if (descs[i].integrator == KHY_INT_VL2) return bfail(KHY_ERR_ARG, "khy_batch_create: Heun integrator only");
     }
     khy_batch *b = new (std::nothrow) khy_batch();
     if (!b) return bfail(KHY_ERR_OOM, "khy_batch_create: host allocation failed");

@@ -62,11 +62,14 @@ static cudaError_t launch_stage_nd(const StageArgs &a, int stage, cudaStream_t s
         case 2: return StageOf<R, ND, 2, S>::launch(a, s);
         case 3: return StageOf<R, ND, 3, S>::launch(a, s);
         case 4: return StageOf<R, ND, 4, S>::launch(a, s);
+        case 5: return StageOf<R, ND, 5, S>::launch(a, s);
+        case 6: return StageOf<R, ND, 6, S>::launch(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-// stage 1, 2: Heun; 3, 4: van Leer predictor and corrector
+// stage 1, 2: Heun; 3, 4: van Leer predictor and corrector; 5, 6: Heun from
+// stored primitives
 template <class R, class S = double>
 static cudaError_t launch_stage_prec(const StageArgs &a, int stage, cudaStream_t s) {
     switch (a.g.ndim) {
@@ -83,7 +86,9 @@ static cudaError_t prepare_nd() {
     if ((e = StageOf<R, ND, 1, S>::prepare()) != cudaSuccess) return e;
     if ((e = StageOf<R, ND, 2, S>::prepare()) != cudaSuccess) return e;
     if ((e = StageOf<R, ND, 3, S>::prepare()) != cudaSuccess) return e;
-    return StageOf<R, ND, 4, S>::prepare();
+    if ((e = StageOf<R, ND, 4, S>::prepare()) != cudaSuccess) return e;
+    if ((e = StageOf<R, ND, 5, S>::prepare()) != cudaSuccess) return e;
+    return StageOf<R, ND, 6, S>::prepare();
 }
 
 template <class R, class S = double>
@@ -206,13 +211,14 @@ static cudaError_t launch_multi_dt_prec(const MultiArgs &a, int ndim, int v, int
 }
 
 template <class R, class S = double>
-static cudaError_t launch_dt_prec(const Geom &g, const double *U, Clock *clk, cudaStream_t s) {
+static cudaError_t launch_dt_prec(const Geom &g, const double *U, Clock *clk, void *W, cudaStream_t s) {
     const long long blocks_needed = (g.ncell + 255) / 256;
     const int blocks = (int)(blocks_needed < 152 * 8 ? blocks_needed : 152 * 8);
+    R *Wr = reinterpret_cast<R *>(W);
     switch (g.ndim) {
-        case 1: dt_kernel<R, 1, S><<<blocks, 256, 0, s>>>(g, U, clk); break;
-        case 2: dt_kernel<R, 2, S><<<blocks, 256, 0, s>>>(g, U, clk); break;
-        case 3: dt_kernel<R, 3, S><<<blocks, 256, 0, s>>>(g, U, clk); break;
+        case 1: dt_kernel<R, 1, S><<<blocks, 256, 0, s>>>(g, U, clk, Wr); break;
+        case 2: dt_kernel<R, 2, S><<<blocks, 256, 0, s>>>(g, U, clk, Wr); break;
+        case 3: dt_kernel<R, 3, S><<<blocks, 256, 0, s>>>(g, U, clk, Wr); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

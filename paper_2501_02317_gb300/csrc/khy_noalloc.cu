@@ -68,7 +68,7 @@ extern "C" khy_status khy_step_noalloc(const khy_mesh_desc *desc, double *U_dev,
     if (!U_dev || !out_dev) return (khy_status)record_error(KHY_ERR_ARG, "khy_step_noalloc: NULL state or output");
     if (desc->prec == KHY_PREC_FP32)
         return (khy_status)record_error(KHY_ERR_ARG, "khy_step_noalloc: FP64 or mixed precision only");
-    if (desc->integrator != KHY_INT_HEUN)
+    if (desc->integrator == KHY_INT_VL2)
         return (khy_status)record_error(KHY_ERR_ARG, "khy_step_noalloc: Heun integrator only");
     if (!(t == t) || !(t_end == t_end)) return (khy_status)record_error(KHY_ERR_ARG, "khy_step_noalloc: t or t_end is NaN");
     const Geom g = geom_of_desc(*desc);
@@ -108,11 +108,13 @@ extern "C" khy_status khy_step_noalloc(const khy_mesh_desc *desc, double *U_dev,
         noalloc_clock_init<<<1, 1, 0, s>>>(clk, t, t_end);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = fp64 ? launch_dt_fp64(g, U_dev, clk, s) : launch_dt_mixed(g, U_dev, clk, s);
+    if (e == cudaSuccess) e = fp64 ? launch_dt_fp64(g, U_dev, clk, nullptr, s) : launch_dt_mixed(g, U_dev, clk, nullptr, s);
     if (e == cudaSuccess) e = launch_clock_step(clk, g, s);
     StageArgs a;
     a.g = g;
     a.clk = clk;
+    a.Win = nullptr;  // stages 1, 2: primitives recovered on the fly
+    a.Wout = nullptr;
     a.cubic = 1;
     for (int d = 1; d < g.ndim; ++d)
         if (g.dx[d] != g.dx[0]) a.cubic = 0;

@@ -2,8 +2,10 @@
 //
 // A khy_sim owns U^n and U^1 (FP64, field-major; with the van Leer
 // integrator the second array holds the half-step primitives W^{n+1/2} in the
-// flux precision instead) and a device Clock.  Steps are recorded once into a
-// CUDA graph of kStepsPerGraph steps and replayed;
+// flux precision instead), for Heun the primitives of U^n and U^1 (flux
+// precision; the stage kernels read them instead of recovering halo cells),
+// and a device Clock.  Steps are recorded once into a CUDA graph of
+// kStepsPerGraph steps and replayed;
 // the time step, the clip to t_end and the stop condition live on the device
 // (clock_kernel), so the host only polls the clock between graph replays.
 //
@@ -143,7 +145,9 @@ struct khy_sim {
     bool own_stream = false;
     double *U = nullptr;   // U^n (FP32 values in the first half for KHY_PREC_FP32)
     double *U1 = nullptr;  // U^1, or W^{n+1/2} (van Leer); also scratch of >= ncell doubles
-    size_t u_bytes = 0, u1_bytes = 0;
+    void *W0 = nullptr;    // Heun: primitives of U^n (written by the CFL kernel and stage 2)
+    void *W1 = nullptr;    // Heun: primitives of U^1 (written by stage 1)
+    size_t u_bytes = 0, u1_bytes = 0, w_bytes = 0;
     Clock *clk = nullptr;
     Clock *clk_host = nullptr;  // pinned mirror for polling
     double *red = nullptr;      // totals partials [2*kTotalsBlocks]
@@ -177,7 +181,7 @@ khy_status validate(const khy_mesh_desc *d) {
     if (!(d->cfl > 0.0 && d->cfl <= 1.0)) return fail(KHY_ERR_ARG, "cfl must be in (0, 1]");
     if (d->prec != KHY_PREC_FP64 && d->prec != KHY_PREC_MIXED && d->prec != KHY_PREC_FP32)
         return fail(KHY_ERR_ARG, "prec must be a khy_prec");
-    if (d->integrator != KHY_INT_HEUN && d->integrator != KHY_INT_VL2)
+    if (d->integrator != KHY_INT_HEUN && d->integrator != KHY_INT_VL2 && d->integrator != KHY_INT_HEUN_LEAN)
         return fail(KHY_ERR_ARG, "integrator must be a khy_integrator");
     if (!(d->rho_floor >= 0.0) || !(d->p_floor >= 0.0)) return fail(KHY_ERR_ARG, "floors must be >= 0");
     return KHY_OK;
@@ -213,8 +217,9 @@ Geom make_geom(const khy_mesh_desc &d) {
     return g;
 }
 
-// Launches sub-step 1 or 2 of the simulation's integrator: Heun stages 1, 2
-// or van Leer stages 3 (predictor: U -> W^{n+1/2} in U1) and 4 (corrector:
+// Launches sub-step 1 or 2 of the simulation's integrator: Heun stages 5, 6
+// (from the stored primitives W0 -> W1 -> W0), lean Heun stages 1, 2, or van
+// Leer stages 3 (predictor: U -> W^{n+1/2} in U1) and 4 (corrector:
 // W^{n+1/2}, U -> U).
 cudaError_t launch_stage(const khy_sim *s, int sub) {
     StageArgs a;
@@ -223,16 +228,32 @@ cudaError_t launch_stage(const khy_sim *s, int sub) {
     a.cubic = 1;
     for (int d = 1; d < s->geom.ndim; ++d)
         if (s->geom.dx[d] != s->geom.dx[0]) a.cubic = 0;
-    if (sub == 1) {
+    a.Win = nullptr;
+    a.Wout = nullptr;
+    int stage = sub;
+    if (s->desc.integrator == KHY_INT_VL2) {
+        stage = sub + 2;
         a.Uin = s->U;
         a.Ubase = s->U;
-        a.Uout = s->U1;
-    } else {
-        a.Uin = s->U1;
-        a.Ubase = s->U;
         a.Uout = s->U;
+        if (sub == 1) a.Wout = s->U1;
+        else a.Win = s->U1;
+    } else {
+        if (sub == 1) {
+            a.Uin = s->U;
+            a.Ubase = s->U;
+            a.Uout = s->U1;
+        } else {
+            a.Uin = s->U1;
+            a.Ubase = s->U;
+            a.Uout = s->U;
+        }
+        if (s->desc.integrator == KHY_INT_HEUN) {
+            stage = sub + 4;
+            a.Win = sub == 1 ? s->W0 : s->W1;
+            a.Wout = sub == 1 ? s->W1 : s->W0;
+        }
     }
-    const int stage = s->desc.integrator == KHY_INT_VL2 ? sub + 2 : sub;
     if (s->desc.prec == KHY_PREC_FP32) return launch_stage_single(a, stage, s->stream);
     return s->desc.prec == KHY_PREC_FP64 ? launch_stage_fp64(a, stage, s->stream)
                                          : launch_stage_mixed(a, stage, s->stream);
@@ -309,9 +330,10 @@ khy_status ensure_wmin(khy_sim *s) {
     if (s->wmin_valid) return KHY_OK;
     clock_wmin_reset_kernel<<<1, 1, 0, s->stream>>>(s->clk);
     KHY_CUDA(cudaGetLastError());
-    if (s->desc.prec == KHY_PREC_FP32) KHY_CUDA(launch_dt_single(s->geom, s->U, s->clk, s->stream));
-    else KHY_CUDA(s->desc.prec == KHY_PREC_FP64 ? launch_dt_fp64(s->geom, s->U, s->clk, s->stream)
-                                                : launch_dt_mixed(s->geom, s->U, s->clk, s->stream));
+    // also stores the primitives of U^n for the Heun stages (W0)
+    if (s->desc.prec == KHY_PREC_FP32) KHY_CUDA(launch_dt_single(s->geom, s->U, s->clk, s->W0, s->stream));
+    else KHY_CUDA(s->desc.prec == KHY_PREC_FP64 ? launch_dt_fp64(s->geom, s->U, s->clk, s->W0, s->stream)
+                                                : launch_dt_mixed(s->geom, s->U, s->clk, s->W0, s->stream));
     s->wmin_valid = true;
     return KHY_OK;
 }
@@ -370,6 +392,11 @@ khy_status khy_create(const khy_mesh_desc *desc, void *cuda_stream, khy_sim **ou
     s->u1_bytes = (desc->integrator == KHY_INT_VL2 && desc->prec != KHY_PREC_FP64) ? bytes / 2 : bytes;
     if (e == cudaSuccess) e = cudaMalloc(&s->U, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&s->U1, s->u1_bytes);
+    if (desc->integrator == KHY_INT_HEUN) {  // primitives of U^n and U^1 in the flux precision
+        s->w_bytes = desc->prec == KHY_PREC_FP64 ? bytes : bytes / 2;
+        if (e == cudaSuccess) e = cudaMalloc(&s->W0, s->w_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&s->W1, s->w_bytes);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&s->clk, sizeof(Clock));
     if (e == cudaSuccess) e = cudaMalloc(&s->red, sizeof(double) * 2 * kTotalsBlocks);
     if (e == cudaSuccess) e = cudaMallocHost(&s->clk_host, sizeof(Clock));
@@ -398,6 +425,8 @@ void khy_destroy(khy_sim *s) {
     drop_graph(s);
     cudaFree(s->U);
     cudaFree(s->U1);
+    cudaFree(s->W0);
+    cudaFree(s->W1);
     cudaFree(s->clk);
     cudaFree(s->red);
     cudaFreeHost(s->clk_host);
@@ -668,8 +697,9 @@ khy_status khy_get_flags(khy_sim *s, unsigned *flags, unsigned long long *floor_
 
 khy_status khy_device_bytes(khy_sim *s, size_t *state_bytes, size_t *total_bytes) {
     if (!s) return fail(KHY_ERR_ARG, "sim is NULL");
-    if (state_bytes) *state_bytes = s->u_bytes + s->u1_bytes;
-    if (total_bytes) *total_bytes = s->u_bytes + s->u1_bytes + sizeof(Clock) + sizeof(double) * 2 * kTotalsBlocks;
+    const size_t st = s->u_bytes + s->u1_bytes + 2 * s->w_bytes;
+    if (state_bytes) *state_bytes = st;
+    if (total_bytes) *total_bytes = st + sizeof(Clock) + sizeof(double) * 2 * kTotalsBlocks;
     return KHY_OK;
 }
 

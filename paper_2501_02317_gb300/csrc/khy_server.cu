@@ -304,7 +304,7 @@ cudaError_t admit(khy_server *s) {
             srv_clock_init_kernel<<<1, 1, 0, s->stream>>>(s->d_clocks + slot, j.t_end);
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) e = launch_dt_mixed(j.geom, s->arena + off, s->d_clocks + slot, s->stream);
+        if (e == cudaSuccess) e = launch_dt_mixed(j.geom, s->arena + off, s->d_clocks + slot, nullptr, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // staging buffer reuse
         j.W.clear();
         j.W.shrink_to_fit();
@@ -473,7 +473,7 @@ khy_status khy_server_submit(khy_server *s, const khy_mesh_desc *desc, const dou
     if (!s || !desc || !W || !job_id) return sfail(KHY_ERR_ARG, "khy_server_submit: NULL argument");
     int st = validate_desc(desc);
     if (st != KHY_OK) return (khy_status)st;
-    if (desc->ndim < 2 || desc->prec != KHY_PREC_MIXED || desc->integrator != KHY_INT_HEUN)
+    if (desc->ndim < 2 || desc->prec != KHY_PREC_MIXED || desc->integrator == KHY_INT_VL2)
         return sfail(KHY_ERR_ARG, "khy_server_submit: the server runs mixed-precision 2D and 3D Heun jobs");
     if (!(t_end > 0.0) || !std::isfinite(t_end)) return sfail(KHY_ERR_ARG, "khy_server_submit: t_end must be > 0");
     Job j;

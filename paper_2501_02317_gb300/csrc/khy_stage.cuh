@@ -17,6 +17,14 @@
 //                    path), in place of U1
 //   stage_kernel 4 : corrector, Un+1 = Un + dt L(W^{n+1/2}) with PLM face
 //                    states of W^{n+1/2}, written over Un, plus the CFL minimum.
+// Single-grid Heun steps keep the primitives of the current state in HBM
+// (in the flux precision) so that no CTA recovers halo cells:
+//   stage_kernel 5 : as stage 1, fluxes from the stored primitives of Un;
+//                    writes U1 and the primitives of U1
+//   stage_kernel 6 : as stage 2, fluxes from the stored primitives of U1;
+//                    writes Un+1 and its primitives.
+// Every stored primitive comes from the same recovery function as an on-the-
+// fly one, so stages 5, 6 give the same bits as stages 1, 2.
 //
 // Work decomposition.  The grid is cut into tiles of TX x TY columns along
 // the slowest ("march") axis -- z in 3D, y in 2D; a 1D grid is one row.  The
@@ -52,9 +60,11 @@ namespace khy {
 
 struct StageArgs {
     Geom g;
-    const double *Uin;    // state the fluxes are computed from (Un, U1; stage 4: W^{n+1/2})
-    const double *Ubase;  // Un (stages 2 and 4); unused in stages 1 and 3
-    double *Uout;         // U1 (stage 1), W^{n+1/2} (stage 3) or Un+1 (stages 2, 4; may alias Ubase)
+    const double *Uin;    // state the stage adds to: Un (1, 3, 5) or U1 (2, 6); unused in 4
+    const double *Ubase;  // Un (stages 2, 4, 6)
+    double *Uout;         // U1 (1, 5) or Un+1 (2, 4, 6; may alias Ubase); unused in 3
+    const void *Win;      // stored primitives the fluxes come from (4: W^{n+1/2}, 5: W^n, 6: W^1)
+    void *Wout;           // primitives written (3: W^{n+1/2}, 5: W^1, 6: W^{n+1})
     Clock *clk;
     int cubic;            // mixed path: all active dx equal (one dt/dx factor)
 };
@@ -86,17 +96,20 @@ struct Tile {
 // paths) or float (all-FP32 path, S = R = float).
 template <class R, int ND, int STAGE, int TX, int TY, class S = double>
 __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__ Uin, const S *Ubase,
-                                            S *Uout, const double (&dtdx)[3], int cubic, int x0, int y0,
+                                            S *Uout, const R *__restrict__ Win, R *Wout,
+                                            const double (&dtdx)[3], int cubic, int x0, int y0,
                                             int k0, int k1, R *sW, R *sFx, R *sFy, unsigned &flags,
                                             unsigned &floors, double &wmin) {
     constexpr bool MIX = std::is_same<R, float>::value;
     constexpr bool SINGLE = std::is_same<S, float>::value;
     static_assert(!SINGLE || MIX, "an FP32 state needs FP32 fluxes");
-    static_assert(STAGE >= 1 && STAGE <= 4, "stages 1, 2 (Heun) and 3, 4 (van Leer)");
-    constexpr bool PLM = STAGE != 3;                  // the predictor uses first-order face states
-    constexpr bool CFL = STAGE == 2 || STAGE == 4;    // last stage of a step: CFL minimum of Un+1
-    constexpr bool FROM_W = STAGE == 4;               // fluxes from stored primitives (type R)
-    constexpr bool TO_W = STAGE == 3;                 // writes primitives (type R) instead of a state
+    static_assert(STAGE >= 1 && STAGE <= 6, "stages 1, 2, 5, 6 (Heun) and 3, 4 (van Leer)");
+    constexpr bool HEUN2 = STAGE == 2 || STAGE == 6;             // Heun average with Ubase
+    constexpr bool PLM = STAGE != 3;                             // the predictor uses first-order face states
+    constexpr bool CFL = STAGE == 2 || STAGE == 4 || STAGE == 6; // last stage of a step: CFL minimum of Un+1
+    constexpr bool FROM_W = STAGE == 4 || STAGE >= 5;            // fluxes from stored primitives (type R)
+    constexpr bool WRITE_U = STAGE != 3;                         // stores the new state
+    constexpr bool WRITE_W = STAGE == 3 || STAGE >= 5;           // stores the new state's primitives
     using T = Tile<ND, TX, TY>;
     constexpr int NV = T::NV, PX = T::PX, PC = T::PC, NT = T::NT;
     constexpr int DM = ND - 1;  // march axis (ND >= 2)
@@ -149,9 +162,8 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
             R w[NV];
             unsigned fl = 0;
             if constexpr (FROM_W) {  // stored primitives: no recovery
-                const R *Wsrc = reinterpret_cast<const R *>(Uin);
 #pragma unroll
-                for (int q = 0; q < NV; ++q) w[q] = __ldg(Wsrc + (long long)q * N + idx);
+                for (int q = 0; q < NV; ++q) w[q] = __ldg(Win + (long long)q * N + idx);
             } else if constexpr (SINGLE) {
                 float u[NV];
 #pragma unroll
@@ -215,143 +227,138 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
         }
     };
 
-    // mixed path: every face of a plane (march-axis faces of all columns, then
-    // the in-plane faces) as a list of tasks, two per packed face_flux2 call;
-    // march fluxes go to sFm[cur & 1], in-plane ones to sFx / sFy.
+    // mixed path: the faces of one plane as three direction-specific task
+    // ranges -- march-axis faces, x faces, y faces -- each padded to whole
+    // warps, so a warp always works on one direction and every rotation is a
+    // compile-time constant.  A task computes two neighbouring faces of one
+    // direction as the two lanes of the packed face_flux2, from one shared
+    // stencil: x and y faces f, f+1 of one row or column share a five-cell
+    // stencil; march faces of the column pair (2c, 2c+1) are read as float2
+    // pairs from the four ring planes.  March fluxes go to sFm[cur & 1],
+    // in-plane ones to sFx / sFy.  The last pair of an x row (faces TX, TX+1)
+    // and of a y column (TY, TY+1) has one valid lane; its idle lane reads
+    // shared memory past the row (other fields or the flux buffers) and
+    // stores nothing.
     R *sFm = sFy + (size_t)NV * T::NYF;  // [2][NV][NT], mixed path only
+    constexpr int XPR = (TX + 2) / 2;                  // x-face pairs per row (faces 0..TX)
+    constexpr int YPC = (ND == 3) ? (TY + 2) / 2 : 0;  // y-face pairs per column (faces 0..TY)
+    constexpr int TY_ = (ND == 3) ? TY : 1;
+    constexpr int NMP = (ND >= 2) ? NT / 2 : 0;        // march-face column pairs
+    constexpr int M_END = (NMP + 31) / 32 * 32;
+    constexpr int X_END = M_END + (XPR * TY_ + 31) / 32 * 32;
+    constexpr int Y_END = X_END + (YPC * TX + 31) / 32 * 32;
+    static_assert(TX % 2 == 0 && (ND != 3 || TY % 2 == 0), "face pairs need even tile sides");
     auto faces_mix = [&](int cur, bool inplane) {
-        constexpr int NTM = (ND >= 2) ? NT : 0;
-        const int ntask = NTM + (inplane ? T::NXF + T::NYF : 0);
         const float *cp = reinterpret_cast<const float *>(sW);
-        // task tau -> plane offsets of its four stencil cells (slot base o*step
-        // plus e0 + o*stride), face direction, destination; false if inactive
-        struct Task {
-            int pbase, pstep, e0, stride, dir, dstride;
-            float *dst;
-        };
-        auto decode = [&](int tau, Task &t) -> bool {
-            if (tau < NTM) {
-                const int ctx = tau % TX, cty = tau / TX;
-                if (ctx >= wact || cty >= hact) return false;
-                t.e0 = (ND == 3) ? (cty + 2) * PX + ctx + 2 : ctx + 2;
-                t.stride = 0;
-                t.pbase = cur - 1;  // planes cur-1 .. cur+2
-                t.pstep = 1;
-                t.dir = DM;
-                t.dst = reinterpret_cast<float *>(sFm) + (size_t)(cur & 1) * NV * NT + tau;
-                t.dstride = NT;
-                return true;
-            }
-            const int f = tau - NTM;
-            t.pbase = cur;
-            t.pstep = 0;
-            if (f < T::NXF) {
-                const int fx = f % (TX + 1), fy = f / (TX + 1);
-                if (fx > wact || fy >= hact) return false;
-                t.e0 = ((ND == 3) ? fy + 2 : 0) * PX + fx;
-                t.stride = 1;
-                t.dir = 0;
-                t.dst = reinterpret_cast<float *>(sFx) + f;
-                t.dstride = T::NXF;
-            } else {
-                const int f2 = f - T::NXF;
-                const int fxx = f2 % TX, fyy = f2 / TX;
-                if (fxx >= wact || fyy > hact) return false;
-                t.e0 = fyy * PX + fxx + 2;
-                t.stride = PX;
-                t.dir = 1;
-                t.dst = reinterpret_cast<float *>(sFy) + f2;
-                t.dstride = T::NYF;
-            }
-            return true;
-        };
-        // lane x of thread t takes task t, lane y task t + half: consecutive
-        // threads read consecutive shared-memory words (no bank conflicts)
-        const int half = (ntask + 1) / 2;
-        for (int pr = tid; pr < half; pr += NT) {
-            Task ta, tb;
-            const bool va = decode(pr, ta);
-            const bool vb = (pr + half < ntask) && decode(pr + half, tb);
-            if (!va && !vb) continue;
-            if (!va) ta = tb;  // an idle lane recomputes its partner's face and stores nothing
-            if (!vb) tb = ta;
-            // gather both stencils already rotated onto their face normals
-            float2 st[4][NV];
+        float *fm = reinterpret_cast<float *>(sFm) + (size_t)(cur & 1) * NV * NT;
+        float *fxo = reinterpret_cast<float *>(sFx);
+        float *fyo = reinterpret_cast<float *>(sFy);
+        const float *plane = cp + (size_t)(cur & 3) * NV * PC;
+        const int ntask = inplane ? Y_END : M_END;
+        for (int k = tid; k < ntask; k += NT) {
+            float2 st[4][NV], Fr[NV];
+            if (k < M_END) {  // march faces between planes cur and cur + 1 of columns 2c, 2c + 1
+                if (k >= NMP) continue;
+                const int col = 2 * k, ctx = col % TX, cty = col / TX;
+                if (ctx >= wact || cty >= hact) continue;
+                const int e = ((ND == 3) ? (cty + 2) * PX : 0) + ctx + 2;
 #pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                const float *pa = cp + (size_t)((ta.pbase + o * ta.pstep) & 3) * NV * PC + ta.e0 + o * ta.stride;
-                const float *pb = cp + (size_t)((tb.pbase + o * tb.pstep) & 3) * NV * PC + tb.e0 + o * tb.stride;
+                for (int o = 0; o < 4; ++o) {
+                    const float *pl = cp + (size_t)((cur - 1 + o) & 3) * NV * PC + e;
+#pragma unroll
+                    for (int j = 0; j < NV; ++j)
+                        st[o][j] = *reinterpret_cast<const float2 *>(pl + (size_t)pk::rot_slot<ND>(DM, j) * PC);
+                }
+                pk::face_flux2<ND, PLM>(st, kc_f, Fr);
 #pragma unroll
                 for (int j = 0; j < NV; ++j)
-                    st[o][j] = make_float2(pa[(size_t)pk::rot_slot<ND>(ta.dir, j) * PC],
-                                           pb[(size_t)pk::rot_slot<ND>(tb.dir, j) * PC]);
-            }
-            float2 Fr[NV];
-            pk::face_flux2<ND, PLM>(st, kc_f, Fr);
-            if (va) {
+                    *reinterpret_cast<float2 *>(fm + (size_t)pk::rot_slot<ND>(DM, j) * NT + col) = Fr[j];
+            } else if (k < X_END) {  // x faces 2p, 2p + 1 of row ty: cells 2p .. 2p + 4
+                const int x = k - M_END;
+                if (x >= XPR * TY_) continue;
+                const int ty_ = x / XPR, p2 = 2 * (x % XPR);
+                if (p2 > wact || ty_ >= hact) continue;
+                const bool vy = p2 + 1 <= wact;
+                const float *pl = plane + ((ND == 3) ? (ty_ + 2) * PX : 0) + p2;
 #pragma unroll
-                for (int j = 0; j < NV; ++j) ta.dst[(size_t)pk::rot_slot<ND>(ta.dir, j) * ta.dstride] = Fr[j].x;
-            }
-            if (vb) {
+                for (int j = 0; j < NV; ++j) {
+                    const float *c = pl + (size_t)j * PC;  // rotation onto x is the identity
+                    const float2 a = *reinterpret_cast<const float2 *>(c);
+                    const float2 b = *reinterpret_cast<const float2 *>(c + 2);
+                    const float2 d = *reinterpret_cast<const float2 *>(c + 4);
+                    st[0][j] = a;
+                    st[1][j] = make_float2(a.y, b.x);
+                    st[2][j] = b;
+                    st[3][j] = make_float2(b.y, d.x);
+                }
+                pk::face_flux2<ND, PLM>(st, kc_f, Fr);
+                float *dst = fxo + ty_ * (TX + 1) + p2;
 #pragma unroll
-                for (int j = 0; j < NV; ++j) tb.dst[(size_t)pk::rot_slot<ND>(tb.dir, j) * tb.dstride] = Fr[j].y;
+                for (int j = 0; j < NV; ++j) {
+                    dst[(size_t)j * T::NXF] = Fr[j].x;
+                    if (vy) dst[(size_t)j * T::NXF + 1] = Fr[j].y;
+                }
+            } else {  // y faces 2p, 2p + 1 of column tx: rows 2p .. 2p + 4
+                const int y = k - X_END;
+                if (y >= YPC * TX) continue;
+                const int tx_ = y % TX, p2 = 2 * (y / TX);
+                if (tx_ >= wact || p2 > hact) continue;
+                const bool vy = p2 + 1 <= hact;
+                const float *pl = plane + p2 * PX + tx_ + 2;
+#pragma unroll
+                for (int j = 0; j < NV; ++j) {
+                    const float *c = pl + (size_t)pk::rot_slot<ND>(1, j) * PC;
+                    const float r0 = c[0], r1 = c[PX], r2 = c[2 * PX], r3 = c[3 * PX], r4 = c[4 * PX];
+                    st[0][j] = make_float2(r0, r1);
+                    st[1][j] = make_float2(r1, r2);
+                    st[2][j] = make_float2(r2, r3);
+                    st[3][j] = make_float2(r3, r4);
+                }
+                pk::face_flux2<ND, PLM>(st, kc_f, Fr);
+                float *dst = fyo + p2 * TX + tx_;
+#pragma unroll
+                for (int j = 0; j < NV; ++j) {
+                    dst[(size_t)pk::rot_slot<ND>(1, j) * T::NYF] = Fr[j].x;
+                    if (vy) dst[(size_t)pk::rot_slot<ND>(1, j) * T::NYF + TX] = Fr[j].y;
+                }
             }
         }
     };
 
-    // conservative update of cell (tx, ty) of plane cur (Sec. 3.3): stages 1,
-    // 3 and 4 add dt L (or dt/2 L) to Un, stage 2 takes the Heun average.
-    // The stage-3 result is only recovered to primitives and stored.
+    // conservative update of cell (tx, ty) of plane cur (Sec. 3.3): stages
+    // 1, 3, 4, 5 add dt L (or dt/2 L) to a state, stages 2, 6 take the Heun
+    // average; then the new state's primitives (stages 3, 5, 6) and its CFL
+    // candidate (last stage of a step).
     auto update_cell = [&](int cur, const R (&Fmlo)[NV], const R (&Fmhi)[NV]) {
         const int gx = x0 + tx;
         const int gy = (ND == 3) ? y0 + ty : (ND == 2 ? cur : 0);
         const int gz = (ND == 3) ? cur : 0;
         if (gx >= g.n[0] || (ND == 3 && gy >= g.n[1])) return;
         const long long idx = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
-        const S *Ucell = FROM_W ? Ubase : Uin;  // the state this stage adds to
-        R *Wout = reinterpret_cast<R *>(Uout);
-        if constexpr (SINGLE) {  // all-FP32: U + dt L(U) in FP32, directions in x, y, z order
-            float un[NV];
-#pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                const float *fx = reinterpret_cast<const float *>(sFx) + (size_t)q * T::NXF + ty * (TX + 1) + tx;
-                const float *fy = reinterpret_cast<const float *>(sFy) + (size_t)q * T::NYF + ty * TX + tx;
-                float acc = __fmul_rn(c32x, __fsub_rn(fx[0], fx[1]));
-                if (ND == 3) acc = __fmaf_rn(c32y, __fsub_rn(fy[0], fy[TX]), acc);
-                if (ND >= 2) acc = __fmaf_rn(c32m, __fsub_rn((float)Fmlo[q], (float)Fmhi[q]), acc);
-                const float u = Ucell[(long long)q * N + idx];
-                float r;
-                if (STAGE != 2) r = __fadd_rn(u, acc);
-                else r = __fmul_rn(0.5f, __fadd_rn(Ubase[(long long)q * N + idx], __fadd_rn(u, acc)));
-                un[q] = r;
-                if (!TO_W) Uout[(long long)q * N + idx] = r;
-            }
-            if (TO_W) {
-                float w[NV];
-                sg::recover<ND>(un, mk, w, flags, floors);
-#pragma unroll
-                for (int q = 0; q < NV; ++q) Wout[(long long)q * N + idx] = w[q];
-            }
-            if (CFL) {
-                const double c = (double)sg::cfl_candidate<ND>(un, mk);
-                wmin = c < wmin ? c : wmin;
-            }
-        } else {
-        double un[NV];
+        const S *Ucell = (STAGE == 4) ? Ubase : Uin;  // the state this stage adds to
+        S un[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
             const R *fx = sFx + (size_t)q * T::NXF + ty * (TX + 1) + tx;
             const R *fy = sFy + (size_t)q * T::NYF + ty * TX + tx;
-            const double u = (double)Ucell[(long long)q * N + idx];
-            double r;
-            if constexpr (!MIX) {
+            S r;
+            if constexpr (SINGLE) {  // all-FP32: U + dt L(U) in FP32, directions in x, y, z order
+                float acc = __fmul_rn(c32x, __fsub_rn(fx[0], fx[1]));
+                if (ND == 3) acc = __fmaf_rn(c32y, __fsub_rn(fy[0], fy[TX]), acc);
+                if (ND >= 2) acc = __fmaf_rn(c32m, __fsub_rn((float)Fmlo[q], (float)Fmhi[q]), acc);
+                const float u = Ucell[(long long)q * N + idx];
+                if (!HEUN2) r = __fadd_rn(u, acc);
+                else r = __fmul_rn(0.5f, __fadd_rn(Ubase[(long long)q * N + idx], __fadd_rn(u, acc)));
+            } else if constexpr (!MIX) {
+                const double u = Ucell[(long long)q * N + idx];
                 // dU = -sum_d (dt/dx_d)(F_hi - F_lo), directions in x, y, z order
                 double acc = 0.0 - dtq[0] * (fx[1] - fx[0]);
                 if (ND == 3) acc = acc - dtq[1] * (fy[TX] - fy[0]);
                 if (ND >= 2) acc = acc - dtq[DM] * (Fmhi[q] - Fmlo[q]);
-                if (STAGE != 2) r = u + acc;
+                if (!HEUN2) r = u + acc;
                 else r = 0.5 * (Ubase[(long long)q * N + idx] + (u + acc));
             } else {
+                const double u = Ucell[(long long)q * N + idx];
                 // F_lo - F_hi per direction, exact as float-float pairs
                 const mx::FF Dx = mx::two_sum(fx[0], -fx[1]);
                 mx::FF Dy = {0.f, 0.f}, Dm = {0.f, 0.f};
@@ -362,7 +369,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                     if (ND == 3) Fs = mx::ff_add(Fs, Dy);
                     if (ND >= 2) Fs = mx::ff_add(Fs, Dm);
                     const double c = dtq[0];
-                    if (STAGE != 2) {
+                    if (!HEUN2) {
                         const double lo = mx::f2d(__fmul_rn(c32, Fs.lo));
                         r = __fma_rn(c, mx::f2d(Fs.hi), __dadd_rn(u, lo));
                     } else {
@@ -375,32 +382,35 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                     double acc = __fma_rn(dtq[0], mx::f2d(Dx.hi), __dmul_rn(dtq[0], mx::f2d(Dx.lo)));
                     if (ND == 3) acc = __fma_rn(dtq[1], mx::f2d(Dy.hi), __fma_rn(dtq[1], mx::f2d(Dy.lo), acc));
                     if (ND >= 2) acc = __fma_rn(dtq[DM], mx::f2d(Dm.hi), __fma_rn(dtq[DM], mx::f2d(Dm.lo), acc));
-                    if (STAGE != 2) r = __dadd_rn(u, acc);
+                    if (!HEUN2) r = __dadd_rn(u, acc);
                     else r = __dmul_rn(0.5, __dadd_rn(Ubase[(long long)q * N + idx], __dadd_rn(u, acc)));
                 }
             }
             un[q] = r;
-            if (!TO_W) Uout[(long long)q * N + idx] = r;
+            if (WRITE_U) Uout[(long long)q * N + idx] = r;
         }
-        if (TO_W) {  // primitives of U^{n+1/2}, floors counted like any recovery
-            R w[NV];
-            if constexpr (MIX) mx::recover<ND>(un, mk, w, flags, floors);
+        R w[NV];
+        if (WRITE_W) {  // primitives of the new state, floors counted like any recovery
+            if constexpr (SINGLE) sg::recover<ND>(un, mk, w, flags, floors);
+            else if constexpr (MIX) mx::recover<ND>(un, mk, w, flags, floors);
             else recover<ND>(un, g, w, flags, floors);
 #pragma unroll
             for (int q = 0; q < NV; ++q) Wout[(long long)q * N + idx] = w[q];
         }
         if (CFL) {  // CFL candidate of the new state for the next step
             double c;
-            if constexpr (MIX) {
+            if constexpr (SINGLE) {
+                c = (double)sg::cfl_candidate<ND>(un, mk);
+            } else if constexpr (MIX) {
                 c = mx::f2d(mx::cfl_candidate<ND>(un, mk));
             } else {
-                double w[NV];
-                unsigned fl = 0;
-                recover<ND>(un, g, w, flags, fl);
+                if (!WRITE_W) {
+                    unsigned fl = 0;
+                    recover<ND>(un, g, w, flags, fl);
+                }
                 c = cfl_candidate<ND>(w, g);
             }
             wmin = c < wmin ? c : wmin;
-        }
         }
     };
 
@@ -494,7 +504,7 @@ __device__ __forceinline__ void reduce_to_clock(Clock *clk, unsigned flags, unsi
     if (tid == 0) {
         if (s_flags) atomicOr(&clk->status, s_flags);
         if (s_floors) atomicAdd(&clk->floor_hits, s_floors);
-        if (STAGE == 2 || STAGE == 4) {
+        if (STAGE == 2 || STAGE == 4 || STAGE == 6) {
             double m = s_wmin[0];
             for (int i = 1; i < NT / 32; ++i) m = s_wmin[i] < m ? s_wmin[i] : m;
             if (m < __longlong_as_double((long long)kInfBits))
@@ -543,7 +553,8 @@ __global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) stage_ke
         const int y0 = (ND == 3) ? (int)(tile / ntx) * TY : 0;
         pos += k1 - k0;
         run_segment<R, ND, STAGE, TX, TY, S>(g, reinterpret_cast<const S *>(a.Uin), reinterpret_cast<const S *>(a.Ubase),
-                                             reinterpret_cast<S *>(a.Uout), dtdx, a.cubic, x0, y0, k0, k1, sW, sFx,
+                                             reinterpret_cast<S *>(a.Uout), reinterpret_cast<const R *>(a.Win),
+                                             reinterpret_cast<R *>(a.Wout), dtdx, a.cubic, x0, y0, k0, k1, sW, sFx,
                                              sFy, flags, floors, wmin);
     }
     reduce_to_clock<STAGE, NT>(a.clk, flags, floors, wmin);
@@ -596,7 +607,8 @@ __global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) multi_st
         const double dtdx[3] = {clk->dtdx[0], clk->dtdx[1], clk->dtdx[2]};
         unsigned flags = 0, floors = 0;
         double wmin = __longlong_as_double((long long)kInfBits);
-        run_segment<R, ND, STAGE, TX, TY>(g, a.Uin + gd->off, a.Ubase + gd->off, a.Uout + gd->off, dtdx, gd->cubic,
+        run_segment<R, ND, STAGE, TX, TY>(g, a.Uin + gd->off, a.Ubase + gd->off, a.Uout + gd->off, nullptr, nullptr,
+                                          dtdx, gd->cubic,
                                           sd.x0, sd.y0, sd.k0, sd.k1, sW, sFx, sFy, flags, floors, wmin);
         reduce_to_clock<STAGE, NT>(clk, flags, floors, wmin);
     }
@@ -648,8 +660,10 @@ __global__ void __launch_bounds__(256) multi_dt_kernel(MultiArgs a, int TX, int 
 
 // CFL minimum over all cells of U (used when the state was set from outside);
 // the same per-cell candidate as the fused one in stage_kernel<..., 2, ...>.
+// When W is not null it also stores the primitives of U (type R) for the
+// stages that read stored primitives.
 template <class R, int ND, class S = double>
-__global__ void __launch_bounds__(256) dt_kernel(Geom g, const double *U, Clock *clk) {
+__global__ void __launch_bounds__(256) dt_kernel(Geom g, const double *U, Clock *clk, R *W) {
     constexpr bool MIX = std::is_same<R, float>::value;
     constexpr bool SINGLE = std::is_same<S, float>::value;
     constexpr int NV = ND + 2;
@@ -666,6 +680,10 @@ __global__ void __launch_bounds__(256) dt_kernel(Geom g, const double *U, Clock 
             for (int q = 0; q < NV; ++q) u[q] = Uf[(long long)q * N + c];
             sg::recover<ND>(u, mk, w, flags, floors);
             m = (double)sg::cfl_candidate<ND>(u, mk);
+            if (W) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) W[(long long)q * N + c] = w[q];
+            }
         } else if constexpr (MIX) {
             double u[NV];
 #pragma unroll
@@ -673,6 +691,10 @@ __global__ void __launch_bounds__(256) dt_kernel(Geom g, const double *U, Clock 
             float w[NV];
             mx::recover<ND>(u, mk, w, flags, floors);
             m = mx::f2d(mx::cfl_candidate<ND>(u, mk));
+            if (W) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) W[(long long)q * N + c] = w[q];
+            }
         } else {
             double u[NV];
 #pragma unroll
@@ -680,6 +702,10 @@ __global__ void __launch_bounds__(256) dt_kernel(Geom g, const double *U, Clock 
             double w[NV];
             recover<ND>(u, g, w, flags, floors);
             m = cfl_candidate<ND>(w, g);
+            if (W) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) W[(long long)q * N + c] = w[q];
+            }
         }
         wmin = m < wmin ? m : wmin;
     }

@@ -35,9 +35,11 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 PREC_FP32 = 2
 
-# time integrators (Sec. 3.3): Heun, memory-optimized van Leer
+# time integrators (Sec. 3.3): Heun, memory-optimized van Leer, and Heun
+# without stored primitives (the same step, less device memory)
 INT_HEUN = 0
 INT_VL2 = 1
+INT_HEUN_LEAN = 2
 
 DEFAULT_FLOOR = 1e-10
 

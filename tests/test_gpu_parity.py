@@ -326,3 +326,33 @@ def test_single_precision_conservation():
             cur = sim.totals()
             assert np.all(np.abs(cur - prev) / scale <= 1e-6), (cur - prev) / scale
             prev = cur
+
+
+# ------------------------------------------------------------ stored primitives vs on-the-fly recovery
+
+@pytest.mark.parametrize("prec", [wl.PREC_FP64, wl.PREC_MIXED, wl.PREC_FP32])
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_stored_primitives_match_lean_step_bitwise(prec, ndim):
+    # the default Heun step reads stored primitives; the lean step recovers
+    # them from the state on the fly with the same function: same bits
+    n = {1: (203, 1, 1), 2: (70, 45, 1), 3: (37, 19, 23)}[ndim]
+    bc = ((wl.BC_REFLECT, wl.BC_OUTFLOW), (wl.BC_PERIODIC, wl.BC_PERIODIC), (wl.BC_FREE, wl.BC_REFLECT))
+    mesh = wl.Mesh(ndim=ndim, n=n, gamma=1.4, cfl=0.3, prec=prec, bc=bc)
+    W = wl.random_smooth(mesh, seed=11 + ndim)
+    Ua, ta, sa, dta = gpu_run(mesh, W, max_steps=9)
+    Ub, tb, sb, dtb = gpu_run(mesh.replace(integrator=wl.INT_HEUN_LEAN), W, max_steps=9)
+    assert sa == sb == 9 and ta == tb and dta == dtb
+    np.testing.assert_array_equal(Ua, Ub)
+
+
+def test_lean_heun_matches_oracle():
+    for prec in (wl.PREC_FP64, wl.PREC_MIXED):
+        mesh = wl.Mesh(ndim=3, n=(37, 11, 9), gamma=5.0 / 3.0, cfl=0.3, prec=prec, integrator=wl.INT_HEUN_LEAN)
+        W = wl.random_jumpy(mesh, seed=57)
+        Uo, _, so, _ = oracle_run(mesh, W, max_steps=4)
+        U, _, s, _ = gpu_run(mesh, W, max_steps=4)
+        assert s == so == 4
+        if prec == wl.PREC_FP64:
+            np.testing.assert_array_equal(U, Uo)
+        check(mesh, U, Uo, prec)
+

@@ -191,19 +191,23 @@ def test_vl2_split_run_equals_straight_run():
 
 def test_vl2_holds_less_device_memory():
     # the second state array becomes primitives in the flux precision:
-    # mixed 40 + 20 bytes per 3D cell instead of 40 + 40 (FP64: unchanged)
+    # mixed 40 + 20 bytes per 3D cell instead of 40 + 40 for the lean Heun
+    # step (FP64: unchanged); the default Heun step also stores the
+    # primitives of U^n and U^1
     from paper_2501_02317_gb300 import khydro
     m = wl.Mesh(ndim=3, n=(16, 12, 10), prec=wl.PREC_MIXED)
     sizes = {}
     for prec in (wl.PREC_FP64, wl.PREC_MIXED, wl.PREC_FP32):
-        for integ in (wl.INT_HEUN, VL):
+        for integ in (wl.INT_HEUN, wl.INT_HEUN_LEAN, VL):
             with khydro.Sim(m.replace(prec=prec, integrator=integ)) as sim:
                 sizes[prec, integ] = sim.device_bytes()[0]
-    cell_bytes = 5 * 8 * 16 * 12 * 10
-    assert sizes[wl.PREC_MIXED, wl.INT_HEUN] == 2 * cell_bytes
-    assert sizes[wl.PREC_MIXED, VL] == cell_bytes + cell_bytes // 2
-    assert sizes[wl.PREC_FP64, VL] == sizes[wl.PREC_FP64, wl.INT_HEUN]
-    assert sizes[wl.PREC_FP32, VL] < sizes[wl.PREC_FP32, wl.INT_HEUN]
+    cb = 5 * 8 * 16 * 12 * 10  # one FP64 state
+    assert sizes[wl.PREC_MIXED, wl.INT_HEUN_LEAN] == 2 * cb
+    assert sizes[wl.PREC_MIXED, wl.INT_HEUN] == 3 * cb
+    assert sizes[wl.PREC_MIXED, VL] == cb + cb // 2
+    assert sizes[wl.PREC_FP64, VL] == sizes[wl.PREC_FP64, wl.INT_HEUN_LEAN] == 2 * cb
+    assert sizes[wl.PREC_FP64, wl.INT_HEUN] == 4 * cb
+    assert sizes[wl.PREC_FP32, VL] < sizes[wl.PREC_FP32, wl.INT_HEUN_LEAN]
 
 
 def test_vl2_profile_and_dt_match_heun_dt():
