@@ -196,8 +196,9 @@ khy_status khy_device_bytes(khy_sim *sim, size_t *state_bytes, size_t *total_byt
 typedef struct khy_batch khy_batch;
 
 /* Validates every descriptor (same ndim and prec for all; KHY_PREC_FP64 or
- * KHY_PREC_MIXED; KHY_INT_HEUN or KHY_INT_HEUN_LEAN, both run as the lean
- * Heun step), allocates the pooled states and the clocks,
+ * KHY_PREC_MIXED; KHY_INT_HEUN or KHY_INT_HEUN_LEAN, both run as the Heun
+ * step with stored primitives), allocates the pooled states (U, U^1 and their
+ * primitives) and the clocks,
  * binds the stream (NULL: a private stream)
  * and builds the segment schedule for the tile variant remembered for this
  * batch shape (variant 0 if none was tuned).  Targets start at t_end = 0, so
@@ -256,9 +257,10 @@ typedef struct khy_server khy_server;
 /* Job states reported by khy_server_poll. */
 enum { KHY_JOB_QUEUED = 0, KHY_JOB_ACTIVE = 1, KHY_JOB_DONE = 2, KHY_JOB_FAILED = 3 };
 
-/* Allocates the arena (hbm_budget_bytes of device memory, split in a U half
- * and a U^1 half), the per-slot clocks (max_slots) and starts the server
- * thread on the current device.  Errors: KHY_ERR_ARG, KHY_ERR_OOM. */
+/* Allocates the arena (hbm_budget_bytes of device memory: U and U^1 in FP64
+ * and their primitives in FP32, 24 bytes per state element), the per-slot
+ * clocks (max_slots) and starts the server thread on the current device.
+ * Errors: KHY_ERR_ARG, KHY_ERR_OOM. */
 khy_status khy_server_create(size_t hbm_budget_bytes, int max_slots, void *cuda_stream, khy_server **out);
 
 /* Stops the server thread (jobs still queued or running are dropped) and
@@ -267,7 +269,7 @@ void khy_server_destroy(khy_server *s);
 
 /* Queues a job: mesh desc (ndim 2 or 3, KHY_PREC_MIXED, a Heun integrator), primitive initial
  * state W (host, count = nvar*ncell doubles, copied), target time t_end > 0.
- * *job_id receives the job's id.  KHY_ERR_BUDGET if the job's two states
+ * *job_id receives the job's id.  KHY_ERR_BUDGET if the job's state arrays
  * cannot fit the arena even when it is empty. */
 khy_status khy_server_submit(khy_server *s, const khy_mesh_desc *desc, const double *W, size_t count, double t_end,
                              long *job_id);

@@ -4,8 +4,10 @@
 // All grids of a batch share one dimensionality and one precision.  Their
 // conserved states are concatenated in one device pool (grid i at offset
 // off_i, each grid field-major as in the single-grid API), U^1 in a second
-// pool; every grid has its own clock, so its own dt (Sec. 3.1) and its own
-// target time.  One Heun step of the whole batch is three launches: a clock
+// pool, and the primitives of U^n and U^1 in two pools of the flux precision
+// at the same offsets (the stage kernels read them instead of recovering halo
+// cells, as a single grid's Heun step does); every grid has its own clock,
+// so its own dt (Sec. 3.1) and its own target time.  One Heun step of the whole batch is three launches: a clock
 // launch (one thread per grid), and one persistent launch per stage that
 // covers every grid through a precomputed segment schedule (tile runs of
 // planes, balanced by cells over the resident CTAs).  K steps are recorded
@@ -113,6 +115,7 @@ struct khy_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     double *U = nullptr, *U1 = nullptr;
+    void *W0 = nullptr, *W1 = nullptr;  // primitives of U and U1 (flux precision)
     GridDesc *d_grids = nullptr;
     Clock *d_clocks = nullptr;
     Clock *h_clocks = nullptr;  // pinned
@@ -146,10 +149,14 @@ MultiArgs args_of(const khy_batch *b, int stage) {
         a.Uin = b->U;
         a.Ubase = b->U;
         a.Uout = b->U1;
+        a.Win = b->W0;
+        a.Wout = b->W1;
     } else {
         a.Uin = b->U1;
         a.Ubase = b->U;
         a.Uout = b->U;
+        a.Win = b->W1;
+        a.Wout = b->W0;
     }
     return a;
 }
@@ -377,8 +384,11 @@ khy_status khy_batch_create(const khy_mesh_desc *descs, int ngrids, void *cuda_s
         e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
         b->own_stream = e == cudaSuccess;
     }
+    const size_t wsize = b->prec == KHY_PREC_FP64 ? sizeof(double) : sizeof(float);
     if (e == cudaSuccess) e = cudaMalloc(&b->U, sizeof(double) * b->pool);
     if (e == cudaSuccess) e = cudaMalloc(&b->U1, sizeof(double) * b->pool);
+    if (e == cudaSuccess) e = cudaMalloc(&b->W0, wsize * b->pool);
+    if (e == cudaSuccess) e = cudaMalloc(&b->W1, wsize * b->pool);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, sizeof(GridDesc) * ngrids);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_clocks, sizeof(Clock) * ngrids);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_clocks, sizeof(Clock) * ngrids);
@@ -418,6 +428,8 @@ void khy_batch_destroy(khy_batch *b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaFree(b->U);
     cudaFree(b->U1);
+    cudaFree(b->W0);
+    cudaFree(b->W1);
     cudaFree(b->d_grids);
     cudaFree(b->d_clocks);
     cudaFree(b->d_segs);

@@ -9,8 +9,8 @@ cudaError_t launch_stage_fp64(const StageArgs &a, int stage, cudaStream_t s) {
     return launch_stage_prec<double>(a, stage, s);
 }
 
-cudaError_t launch_dt_fp64(const Geom &g, const double *U, Clock *clk, void *W, cudaStream_t s) {
-    return launch_dt_prec<double>(g, U, clk, W, s);
+cudaError_t launch_dt_fp64(const Geom &g, const double *U, Clock *clk, void *W, int from_state, cudaStream_t s) {
+    return launch_dt_prec<double>(g, U, clk, W, from_state, s);
 }
 
 cudaError_t prepare_fp64(int ndim) { return prepare_prec<double>(ndim); }

@@ -12,17 +12,18 @@ namespace khy {
 
 // Stage kernel (stage 1, 2: Heun; 3, 4: van Leer predictor and corrector;
 // 5, 6: Heun from stored primitives) and CFL-minimum kernel for each
-// precision; the CFL kernel also stores the primitives when W is not null.
+// precision; the CFL kernel also stores the primitives when W is not null,
+// and with from_state uses the van Leer corrector's estimate (mixed / FP32).
 // khy_fp64.cu builds the double instantiations with -fmad=false; khy_mixed.cu
 // builds the float (mixed) instantiations.
 cudaError_t launch_stage_fp64(const StageArgs &a, int stage, cudaStream_t s);
-cudaError_t launch_dt_fp64(const Geom &g, const double *U, Clock *clk, void *W, cudaStream_t s);
+cudaError_t launch_dt_fp64(const Geom &g, const double *U, Clock *clk, void *W, int from_state, cudaStream_t s);
 cudaError_t launch_stage_mixed(const StageArgs &a, int stage, cudaStream_t s);
-cudaError_t launch_dt_mixed(const Geom &g, const double *U, Clock *clk, void *W, cudaStream_t s);
+cudaError_t launch_dt_mixed(const Geom &g, const double *U, Clock *clk, void *W, int from_state, cudaStream_t s);
 // all-FP32 path (khy_single.cu): the state pointers in StageArgs and U point
 // to FP32 arrays (the buffers are reinterpreted)
 cudaError_t launch_stage_single(const StageArgs &a, int stage, cudaStream_t s);
-cudaError_t launch_dt_single(const Geom &g, const double *U, Clock *clk, void *W, cudaStream_t s);
+cudaError_t launch_dt_single(const Geom &g, const double *U, Clock *clk, void *W, int from_state, cudaStream_t s);
 cudaError_t prepare_single(int ndim);
 
 // Many-grid (batched / served) launches.  A variant is a tile shape; the

@@ -151,9 +151,10 @@ struct VT {
 template <class R, int ND, int V, int STAGE>
 using MultiOf = MultiLaunch<R, ND, STAGE, VT<ND, V>::tx, VT<ND, V>::ty>;
 
+// batch stage 1 / 2: the Heun stages that read stored primitives (5, 6)
 template <class R, int ND, int V>
 static cudaError_t multi_stage_v(const MultiArgs &a, int stage, int nblocks, cudaStream_t s) {
-    return stage == 1 ? MultiOf<R, ND, V, 1>::launch(a, nblocks, s) : MultiOf<R, ND, V, 2>::launch(a, nblocks, s);
+    return stage == 1 ? MultiOf<R, ND, V, 5>::launch(a, nblocks, s) : MultiOf<R, ND, V, 6>::launch(a, nblocks, s);
 }
 
 template <class R>
@@ -174,8 +175,8 @@ static cudaError_t launch_multi_stage_prec(const MultiArgs &a, int ndim, int v, 
 
 template <class R, int ND, int V>
 static int multi_resident_v() {
-    using L1 = MultiOf<R, ND, V, 1>;
-    using L2 = MultiOf<R, ND, V, 2>;
+    using L1 = MultiOf<R, ND, V, 5>;
+    using L2 = MultiOf<R, ND, V, 6>;
     if (L1::resident() == 0 && L1::prepare() != cudaSuccess) return 0;
     if (L2::resident() == 0 && L2::prepare() != cudaSuccess) return 0;
     return L1::resident() < L2::resident() ? L1::resident() : L2::resident();
@@ -196,29 +197,32 @@ static int multi_resident_prec(int ndim, int v) {
     }
 }
 
+// CFL minimum of every grid; stores the primitives of a.Uin into the pool a.Win
 template <class R>
 static cudaError_t launch_multi_dt_prec(const MultiArgs &a, int ndim, int v, int nblocks, cudaStream_t s) {
     const VariantTile t = variant_tile(ndim, v);
     if (t.tx == 0) return cudaErrorInvalidValue;
     if (nblocks <= 0) return cudaSuccess;
+    R *W = reinterpret_cast<R *>(const_cast<void *>(a.Win));
     switch (ndim) {
-        case 1: multi_dt_kernel<R, 1><<<nblocks, 256, 0, s>>>(a, t.tx, t.ty); break;
-        case 2: multi_dt_kernel<R, 2><<<nblocks, 256, 0, s>>>(a, t.tx, t.ty); break;
-        case 3: multi_dt_kernel<R, 3><<<nblocks, 256, 0, s>>>(a, t.tx, t.ty); break;
+        case 1: multi_dt_kernel<R, 1><<<nblocks, 256, 0, s>>>(a, t.tx, t.ty, W); break;
+        case 2: multi_dt_kernel<R, 2><<<nblocks, 256, 0, s>>>(a, t.tx, t.ty, W); break;
+        case 3: multi_dt_kernel<R, 3><<<nblocks, 256, 0, s>>>(a, t.tx, t.ty, W); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 template <class R, class S = double>
-static cudaError_t launch_dt_prec(const Geom &g, const double *U, Clock *clk, void *W, cudaStream_t s) {
+static cudaError_t launch_dt_prec(const Geom &g, const double *U, Clock *clk, void *W, int from_state,
+                                  cudaStream_t s) {
     const long long blocks_needed = (g.ncell + 255) / 256;
     const int blocks = (int)(blocks_needed < 152 * 8 ? blocks_needed : 152 * 8);
     R *Wr = reinterpret_cast<R *>(W);
     switch (g.ndim) {
-        case 1: dt_kernel<R, 1, S><<<blocks, 256, 0, s>>>(g, U, clk, Wr); break;
-        case 2: dt_kernel<R, 2, S><<<blocks, 256, 0, s>>>(g, U, clk, Wr); break;
-        case 3: dt_kernel<R, 3, S><<<blocks, 256, 0, s>>>(g, U, clk, Wr); break;
+        case 1: dt_kernel<R, 1, S><<<blocks, 256, 0, s>>>(g, U, clk, Wr, from_state); break;
+        case 2: dt_kernel<R, 2, S><<<blocks, 256, 0, s>>>(g, U, clk, Wr, from_state); break;
+        case 3: dt_kernel<R, 3, S><<<blocks, 256, 0, s>>>(g, U, clk, Wr, from_state); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

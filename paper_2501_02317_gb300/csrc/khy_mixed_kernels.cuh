@@ -14,8 +14,8 @@
 //     update U + c (S_hi + S_lo) costs two FP64 operations in stage 1 and
 //     three in stage 2 (the Heun average), and each face flux still enters
 //     its two cells with opposite signs to full FP64 precision.
-//   * The CFL minimum for the next step is taken in FP32 from the new state,
-//     with an FP64 internal energy only where E - ke cancels.
+//   * The CFL minimum for the next step is taken in FP32 from the recovered
+//     primitives of the new state.
 //
 // The stage kernel that uses these functions is khy_stage.cuh.
 #pragma once
@@ -41,6 +41,31 @@ __device__ __forceinline__ float d2f(double x) {
     if (e >= 255) f = sign | 0x7F800000u | ((((hi & 0x7FF00000u) == 0x7FF00000u) && ((hi & 0xFFFFFu) | lo)) ? 0x400000u : 0u);
     return __uint_as_float(f);
 }
+
+// float -> double for the flux sums and reciprocals of the update: exact for
+// zero and normal floats; a subnormal float (below 1.2e-38) maps to a double
+// of the same sign below 2^-126, and inf / NaN to a finite double of magnitude
+// >= 2^128 (a non-finite flux only comes from a state the recovery has
+// already flagged).  Four integer operations instead of the FP64 pipe's
+// conversion.
+__device__ __forceinline__ double f2d_fast(float x) {
+    const unsigned f = __float_as_uint(x);
+    const unsigned a = f & 0x7FFFFFFFu;
+    // exponent re-bias 127 -> 1023 is + (896 << 20) on the high word
+    const unsigned hi = (a == 0u ? 0u : (a >> 3) + 0x38000000u) | (f & 0x80000000u);
+    return __hiloint2double((int)hi, (int)(f << 29));
+}
+
+// |x| -> float rounded toward zero, for estimates only (the CFL candidate of
+// the van Leer corrector): magnitudes below 2^-126 flush to zero; |x| must
+// stay below 2^128.
+__device__ __forceinline__ float abs_d2f_rz(double x) {
+    const unsigned a = (unsigned)__double2hiint(x) & 0x7FFFFFFFu;
+    const unsigned lo = (unsigned)__double2loint(x);
+    const unsigned f = ((a - 0x38000000u) << 3) | (lo >> 29);
+    return __uint_as_float(a < 0x38100000u ? 0u : f);
+}
+__device__ __forceinline__ float abs_d2f_rz(float x) { return fabsf(x); }
 
 // float -> double, exact for normal floats (subnormals flush to zero).
 __device__ __forceinline__ double f2d(float x) {
@@ -118,8 +143,8 @@ __device__ __forceinline__ void recover(const double (&u)[ND + 2], const MixCons
         ++floors;
     }
     const float rho32 = d2f(rho);
-    const float r32 = __frcp_rn(rho32);
-    double r = f2d(r32);
+    const float r32 = __fdividef(1.0f, rho32);  // ~1 ulp; the FP64 Newton step below squares its error
+    double r = f2d_fast(r32);
     const double e = __fma_rn(-rho, r, 1.0);  // one Newton step: |1 - rho r| ~ 2^-46
     r = __fma_rn(r, e, r);
     double msq = __dmul_rn(u[1], u[1]);
@@ -139,37 +164,57 @@ __device__ __forceinline__ void recover(const double (&u)[ND + 2], const MixCons
     w[ND + 1] = p;
 }
 
-// CFL candidate min_d dx_d / (|v_d| + c_s) in FP32; the internal energy falls
-// back to FP64 where E - ke cancels by more than a factor of four.  Written
-// with explicit round-to-nearest intrinsics (no contraction), so every kernel
-// that calls it produces the same bits for the same state.
+// CFL candidate min_d dx_d / (|v_d| + c_s), c_s = sqrt(gamma p / rho), of one
+// cell from its recovered FP32 primitives (Sec. 3.1: the step length comes
+// out of the variable conversion).  An estimate: division and square root
+// use the special-function unit.  Written with explicit round-to-nearest
+// intrinsics (no contraction), so every kernel that calls it produces the
+// same bits for the same primitives.
 template <int ND>
-__device__ __forceinline__ float cfl_candidate(const double (&u)[ND + 2], const MixConsts &k) {
-    float rho = d2f(u[0]);
+__device__ __forceinline__ float cfl_from_prim(const float (&w)[ND + 2], const MixConsts &k) {
+    const float c = rroot(rdiv(__fmul_rn(k.gamma, w[ND + 1]), w[0]));
+    float m = rdiv(k.dx[0], __fadd_rn(fabsf(w[1]), c));
+#pragma unroll
+    for (int d = 1; d < ND; ++d) {
+        const float t = rdiv(k.dx[d], __fadd_rn(fabsf(w[1 + d]), c));
+        m = t < m ? t : m;
+    }
+    return m;
+}
+
+// CFL candidate straight from a conserved state (FP64 or FP32 storage), for
+// the van Leer corrector, which stores no primitives of the new state: FP32
+// estimate of rho, |v_d| and p; with an FP64 state the internal energy falls
+// back to FP64 where E - ke cancels by more than a factor of four.
+template <int ND, class S>
+__device__ __forceinline__ float cfl_from_state(const S (&u)[ND + 2], const MixConsts &k) {
+    float rho = abs_d2f_rz(u[0]);
     if (!(rho >= k.rho_floor)) rho = k.rho_floor;
-    const float r = __frcp_rn(rho);
+    const float r = __fdividef(1.0f, rho);
     float v[ND];
     float vsq = 0.f;
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-        v[d] = __fmul_rn(d2f(u[1 + d]), r);
+        v[d] = __fmul_rn(abs_d2f_rz(u[1 + d]), r);
         vsq = __fmaf_rn(v[d], v[d], vsq);
     }
-    const float E = d2f(u[ND + 1]);
+    const float E = abs_d2f_rz(u[ND + 1]);
     float eint = __fsub_rn(E, __fmul_rn(__fmul_rn(0.5f, rho), vsq));
-    if (eint < __fmul_rn(0.25f, E)) {
-        double msq = __dmul_rn(u[1], u[1]);
+    if constexpr (sizeof(S) == 8) {
+        if (eint < __fmul_rn(0.25f, E)) {
+            double msq = __dmul_rn(u[1], u[1]);
 #pragma unroll
-        for (int d = 1; d < ND; ++d) msq = __fma_rn(u[1 + d], u[1 + d], msq);
-        eint = d2f(__dsub_rn(u[ND + 1], __ddiv_rn(__dmul_rn(0.5, msq), u[0])));
+            for (int d = 1; d < ND; ++d) msq = __fma_rn(u[1 + d], u[1 + d], msq);
+            eint = d2f(__dsub_rn(u[ND + 1], __ddiv_rn(__dmul_rn(0.5, msq), u[0])));
+        }
     }
     float p = __fmul_rn(k.gm1, eint);
     if (!(p >= k.p_floor)) p = k.p_floor;
-    const float c = __fsqrt_rn(__fmul_rn(__fmul_rn(k.gamma, p), r));
-    float m = __fdiv_rn(k.dx[0], __fadd_rn(fabsf(v[0]), c));
+    const float c = rroot(__fmul_rn(__fmul_rn(k.gamma, p), r));
+    float m = rdiv(k.dx[0], __fadd_rn(v[0], c));
 #pragma unroll
     for (int d = 1; d < ND; ++d) {
-        const float t = __fdiv_rn(k.dx[d], __fadd_rn(fabsf(v[d]), c));
+        const float t = rdiv(k.dx[d], __fadd_rn(v[d], c));
         m = t < m ? t : m;
     }
     return m;

@@ -108,7 +108,7 @@ extern "C" khy_status khy_step_noalloc(const khy_mesh_desc *desc, double *U_dev,
         noalloc_clock_init<<<1, 1, 0, s>>>(clk, t, t_end);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = fp64 ? launch_dt_fp64(g, U_dev, clk, nullptr, s) : launch_dt_mixed(g, U_dev, clk, nullptr, s);
+    if (e == cudaSuccess) e = fp64 ? launch_dt_fp64(g, U_dev, clk, nullptr, 0, s) : launch_dt_mixed(g, U_dev, clk, nullptr, 0, s);
     if (e == cudaSuccess) e = launch_clock_step(clk, g, s);
     StageArgs a;
     a.g = g;

@@ -331,9 +331,10 @@ khy_status ensure_wmin(khy_sim *s) {
     clock_wmin_reset_kernel<<<1, 1, 0, s->stream>>>(s->clk);
     KHY_CUDA(cudaGetLastError());
     // also stores the primitives of U^n for the Heun stages (W0)
-    if (s->desc.prec == KHY_PREC_FP32) KHY_CUDA(launch_dt_single(s->geom, s->U, s->clk, s->W0, s->stream));
-    else KHY_CUDA(s->desc.prec == KHY_PREC_FP64 ? launch_dt_fp64(s->geom, s->U, s->clk, s->W0, s->stream)
-                                                : launch_dt_mixed(s->geom, s->U, s->clk, s->W0, s->stream));
+    const int vl = s->desc.integrator == KHY_INT_VL2;
+    if (s->desc.prec == KHY_PREC_FP32) KHY_CUDA(launch_dt_single(s->geom, s->U, s->clk, s->W0, vl, s->stream));
+    else KHY_CUDA(s->desc.prec == KHY_PREC_FP64 ? launch_dt_fp64(s->geom, s->U, s->clk, s->W0, vl, s->stream)
+                                                : launch_dt_mixed(s->geom, s->U, s->clk, s->W0, vl, s->stream));
     s->wmin_valid = true;
     return KHY_OK;
 }

@@ -3,8 +3,9 @@
 // Jobs (one grid each: 2D or 3D, any size, own target time) are submitted from
 // any host thread and queued.  A server thread owns the GPU work:
 //   * admission: a queued job is admitted as soon as a slot and HBM for its
-//     two states (U and U^1) are free in the server's arena (one allocation
-//     of hbm_budget bytes made at creation; first-fit with coalescing); its
+//     state arrays (U and U^1 in FP64, the primitives of both in FP32) are free
+//     in the server's arena (one allocation of hbm_budget bytes made at
+//     creation, 24 bytes per state element; first-fit with coalescing); its
 //     initial state is copied in and converted on the device, its clock set;
 //   * stepping: every iteration runs a few Heun steps of every active job of
 //     one dimensionality in one persistent launch per stage (the batch engine
@@ -148,8 +149,8 @@ struct khy_server {
     int max_slots = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    double *arena = nullptr;  // [U half | U1 half]
-    size_t half = 0;          // doubles per half
+    double *arena = nullptr;  // [U | U1 (half doubles each) | W0 | W1 (half floats each)]
+    size_t half = 0;          // elements per region
     Arena alloc;
     GridDesc *d_grids = nullptr;  // per slot
     Clock *d_clocks = nullptr;    // per slot
@@ -190,14 +191,19 @@ MultiArgs srv_args(const khy_server *s, int nd, int stage) {
     a.cta_seg = s->d_cta[nd];
     a.clocks = s->d_clocks;
     double *U = s->arena, *U1 = s->arena + s->half;
+    float *W0 = reinterpret_cast<float *>(s->arena + 2 * s->half), *W1 = W0 + s->half;
     if (stage == 1) {
         a.Uin = U;
         a.Ubase = U;
         a.Uout = U1;
+        a.Win = W0;
+        a.Wout = W1;
     } else {
         a.Uin = U1;
         a.Ubase = U;
         a.Uout = U;
+        a.Win = W1;
+        a.Wout = W0;
     }
     return a;
 }
@@ -304,7 +310,9 @@ cudaError_t admit(khy_server *s) {
             srv_clock_init_kernel<<<1, 1, 0, s->stream>>>(s->d_clocks + slot, j.t_end);
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) e = launch_dt_mixed(j.geom, s->arena + off, s->d_clocks + slot, nullptr, s->stream);
+        if (e == cudaSuccess)  // also stores the job's primitives in W0
+            e = launch_dt_mixed(j.geom, s->arena + off, s->d_clocks + slot,
+                                reinterpret_cast<float *>(s->arena + 2 * s->half) + off, 0, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // staging buffer reuse
         j.W.clear();
         j.W.shrink_to_fit();
@@ -404,7 +412,8 @@ khy_status khy_server_create(size_t hbm_budget_bytes, int max_slots, void *cuda_
     if (!s) return sfail(KHY_ERR_OOM, "khy_server_create: host allocation failed");
     s->budget = hbm_budget_bytes;
     s->max_slots = max_slots;
-    s->half = (hbm_budget_bytes / sizeof(double)) / 2 & ~size_t(31);
+    // 2 doubles + 2 floats per state element
+    s->half = (hbm_budget_bytes / (2 * sizeof(double) + 2 * sizeof(float))) & ~size_t(31);
     s->alloc.init(s->half);
     s->h_grids.resize(max_slots);
     s->slot_job.assign(max_slots, -1);
@@ -417,7 +426,7 @@ khy_status khy_server_create(size_t hbm_budget_bytes, int max_slots, void *cuda_
             s->own_stream = e == cudaSuccess;
         }
     }
-    if (e == cudaSuccess) e = cudaMalloc(&s->arena, sizeof(double) * 2 * s->half);
+    if (e == cudaSuccess) e = cudaMalloc(&s->arena, (2 * sizeof(double) + 2 * sizeof(float)) * s->half);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_grids, sizeof(GridDesc) * max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_clocks, sizeof(Clock) * max_slots);
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_clocks, sizeof(Clock) * max_slots);
@@ -483,7 +492,7 @@ khy_status khy_server_submit(khy_server *s, const khy_mesh_desc *desc, const dou
     if (count != n) return sfail(KHY_ERR_ARG, "khy_server_submit: count must be nvar*ncell");
     j.len = 2 * n;  // U and U^1
     if (((n + 31) & ~size_t(31)) > s->half)
-        return sfail(KHY_ERR_BUDGET, "khy_server_submit: the job's two states exceed the HBM budget");
+        return sfail(KHY_ERR_BUDGET, "khy_server_submit: the job's state arrays exceed the HBM budget");
     j.W.assign(W, W + n);
     j.t_end = t_end;
     std::lock_guard<std::mutex> lk(s->mu);

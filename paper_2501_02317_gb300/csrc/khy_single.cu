@@ -9,8 +9,8 @@ cudaError_t launch_stage_single(const StageArgs &a, int stage, cudaStream_t s) {
     return launch_stage_prec<float, float>(a, stage, s);
 }
 
-cudaError_t launch_dt_single(const Geom &g, const double *U, Clock *clk, void *W, cudaStream_t s) {
-    return launch_dt_prec<float, float>(g, U, clk, W, s);
+cudaError_t launch_dt_single(const Geom &g, const double *U, Clock *clk, void *W, int from_state, cudaStream_t s) {
+    return launch_dt_prec<float, float>(g, U, clk, W, from_state, s);
 }
 
 cudaError_t prepare_single(int ndim) { return prepare_prec<float, float>(ndim); }

@@ -40,31 +40,5 @@ __device__ __forceinline__ void recover(const float (&u)[ND + 2], const mx::MixC
     w[ND + 1] = p;
 }
 
-// CFL candidate min_d dx_d / (|v_d| + c_s) from an FP32 state.
-template <int ND>
-__device__ __forceinline__ float cfl_candidate(const float (&u)[ND + 2], const mx::MixConsts &k) {
-    float rho = u[0];
-    if (!(rho >= k.rho_floor)) rho = k.rho_floor;
-    const float r = __frcp_rn(rho);
-    float v[ND];
-    float vsq = 0.f;
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
-        v[d] = __fmul_rn(u[1 + d], r);
-        vsq = __fmaf_rn(v[d], v[d], vsq);
-    }
-    const float eint = __fsub_rn(u[ND + 1], __fmul_rn(__fmul_rn(0.5f, rho), vsq));
-    float p = __fmul_rn(k.gm1, eint);
-    if (!(p >= k.p_floor)) p = k.p_floor;
-    const float c = __fsqrt_rn(__fmul_rn(__fmul_rn(k.gamma, p), r));
-    float m = __fdiv_rn(k.dx[0], __fadd_rn(fabsf(v[0]), c));
-#pragma unroll
-    for (int d = 1; d < ND; ++d) {
-        const float t = __fdiv_rn(k.dx[d], __fadd_rn(fabsf(v[d]), c));
-        m = t < m ? t : m;
-    }
-    return m;
-}
-
 }  // namespace sg
 }  // namespace khy

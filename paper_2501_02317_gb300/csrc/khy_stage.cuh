@@ -130,7 +130,8 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     for (int d = 0; d < 3; ++d) dtq[d] = STAGE == 3 ? 0.5 * dtdx[d] : dtdx[d];
     // dt/dx and dt/(2 dx) rounded to FP32 once (they scale the small
     // low-order part of the flux sums in the mixed update)
-    const float c32 = mx::d2f(dtq[0]), hc32 = mx::d2f(0.5 * dtq[0]);
+    const double hcd = 0.5 * dtq[0];
+    const float c32 = mx::d2f(dtq[0]), hc32 = mx::d2f(hcd);
     const float c32x = c32, c32y = mx::d2f(dtq[1]), c32m = mx::d2f(dtq[DM < 0 ? 0 : DM]);
 
     // tiles whose halo box lies inside the grid skip the ghost-zone index map
@@ -368,20 +369,18 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                     mx::FF Fs = Dx;
                     if (ND == 3) Fs = mx::ff_add(Fs, Dy);
                     if (ND >= 2) Fs = mx::ff_add(Fs, Dm);
-                    const double c = dtq[0];
                     if (!HEUN2) {
-                        const double lo = mx::f2d(__fmul_rn(c32, Fs.lo));
-                        r = __fma_rn(c, mx::f2d(Fs.hi), __dadd_rn(u, lo));
+                        const double lo = mx::f2d_fast(__fmul_rn(c32, Fs.lo));
+                        r = __fma_rn(dtq[0], mx::f2d_fast(Fs.hi), __dadd_rn(u, lo));
                     } else {
-                        const double hc = 0.5 * c;
-                        const double lo = mx::f2d(__fmul_rn(hc32, Fs.lo));
+                        const double lo = mx::f2d_fast(__fmul_rn(hc32, Fs.lo));
                         const double A = __dadd_rn(Ubase[(long long)q * N + idx], u);
-                        r = __fma_rn(hc, mx::f2d(Fs.hi), __fma_rn(0.5, A, lo));
+                        r = __fma_rn(hcd, mx::f2d_fast(Fs.hi), __fma_rn(0.5, A, lo));
                     }
                 } else {
-                    double acc = __fma_rn(dtq[0], mx::f2d(Dx.hi), __dmul_rn(dtq[0], mx::f2d(Dx.lo)));
-                    if (ND == 3) acc = __fma_rn(dtq[1], mx::f2d(Dy.hi), __fma_rn(dtq[1], mx::f2d(Dy.lo), acc));
-                    if (ND >= 2) acc = __fma_rn(dtq[DM], mx::f2d(Dm.hi), __fma_rn(dtq[DM], mx::f2d(Dm.lo), acc));
+                    double acc = __fma_rn(dtq[0], mx::f2d_fast(Dx.hi), __dmul_rn(dtq[0], mx::f2d_fast(Dx.lo)));
+                    if (ND == 3) acc = __fma_rn(dtq[1], mx::f2d_fast(Dy.hi), __fma_rn(dtq[1], mx::f2d_fast(Dy.lo), acc));
+                    if (ND >= 2) acc = __fma_rn(dtq[DM], mx::f2d_fast(Dm.hi), __fma_rn(dtq[DM], mx::f2d_fast(Dm.lo), acc));
                     if (!HEUN2) r = __dadd_rn(u, acc);
                     else r = __dmul_rn(0.5, __dadd_rn(Ubase[(long long)q * N + idx], __dadd_rn(u, acc)));
                 }
@@ -389,27 +388,26 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
             un[q] = r;
             if (WRITE_U) Uout[(long long)q * N + idx] = r;
         }
+        // CFL estimate of the van Leer corrector (mixed / FP32): straight from
+        // the state, which it does not recover
+        constexpr bool CFL_STATE = MIX && STAGE == 4;
         R w[NV];
-        if (WRITE_W) {  // primitives of the new state, floors counted like any recovery
-            if constexpr (SINGLE) sg::recover<ND>(un, mk, w, flags, floors);
-            else if constexpr (MIX) mx::recover<ND>(un, mk, w, flags, floors);
-            else recover<ND>(un, g, w, flags, floors);
+        if (WRITE_W || (CFL && !CFL_STATE)) {  // primitives of the new state
+            unsigned fl = 0;   // floors count once per stored recovery
+            if constexpr (SINGLE) sg::recover<ND>(un, mk, w, flags, fl);
+            else if constexpr (MIX) mx::recover<ND>(un, mk, w, flags, fl);
+            else recover<ND>(un, g, w, flags, fl);
+            if (WRITE_W) {
+                floors += fl;
 #pragma unroll
-            for (int q = 0; q < NV; ++q) Wout[(long long)q * N + idx] = w[q];
+                for (int q = 0; q < NV; ++q) Wout[(long long)q * N + idx] = w[q];
+            }
         }
         if (CFL) {  // CFL candidate of the new state for the next step
             double c;
-            if constexpr (SINGLE) {
-                c = (double)sg::cfl_candidate<ND>(un, mk);
-            } else if constexpr (MIX) {
-                c = mx::f2d(mx::cfl_candidate<ND>(un, mk));
-            } else {
-                if (!WRITE_W) {
-                    unsigned fl = 0;
-                    recover<ND>(un, g, w, flags, fl);
-                }
-                c = cfl_candidate<ND>(w, g);
-            }
+            if constexpr (CFL_STATE) c = mx::f2d(mx::cfl_from_state<ND>(un, mk));
+            else if constexpr (MIX) c = mx::f2d(mx::cfl_from_prim<ND>(w, mk));
+            else c = cfl_candidate<ND>(w, g);
             wmin = c < wmin ? c : wmin;
         }
     };
@@ -583,9 +581,11 @@ struct MultiArgs {
     const GridDesc *grids;
     const SegDesc *segs;
     const int *cta_seg;  // CTA b runs segments [cta_seg[b], cta_seg[b + 1])
-    const double *Uin;   // pool the fluxes are computed from (U or U1)
-    const double *Ubase; // U pool (stage 2 average)
-    double *Uout;        // U1 pool (stage 1) or U pool (stage 2)
+    const double *Uin;   // pool the stage adds to (U or U1)
+    const double *Ubase; // U pool (Heun average)
+    double *Uout;        // U1 pool (stage 5) or U pool (stage 6)
+    const void *Win;     // primitive pool the fluxes come from (W0 or W1, flux precision)
+    void *Wout;          // primitive pool written (W1 or W0)
     Clock *clocks;       // one per grid
 };
 
@@ -607,17 +607,19 @@ __global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) multi_st
         const double dtdx[3] = {clk->dtdx[0], clk->dtdx[1], clk->dtdx[2]};
         unsigned flags = 0, floors = 0;
         double wmin = __longlong_as_double((long long)kInfBits);
-        run_segment<R, ND, STAGE, TX, TY>(g, a.Uin + gd->off, a.Ubase + gd->off, a.Uout + gd->off, nullptr, nullptr,
-                                          dtdx, gd->cubic,
+        run_segment<R, ND, STAGE, TX, TY>(g, a.Uin + gd->off, a.Ubase + gd->off, a.Uout + gd->off,
+                                          reinterpret_cast<const R *>(a.Win) + gd->off,
+                                          reinterpret_cast<R *>(a.Wout) + gd->off, dtdx, gd->cubic,
                                           sd.x0, sd.y0, sd.k0, sd.k1, sW, sFx, sFy, flags, floors, wmin);
         reduce_to_clock<STAGE, NT>(clk, flags, floors, wmin);
     }
 }
 
 // Per-grid CFL minimum of every grid over the same segments (after the
-// states were set from outside).
+// states were set from outside); also stores every cell's primitives in the
+// pool W (flux precision) for the stages that read stored primitives.
 template <class R, int ND>
-__global__ void __launch_bounds__(256) multi_dt_kernel(MultiArgs a, int TX, int TY) {
+__global__ void __launch_bounds__(256) multi_dt_kernel(MultiArgs a, int TX, int TY, R *W) {
     constexpr bool MIX = std::is_same<R, float>::value;
     constexpr int NV = ND + 2;
     const int sb = a.cta_seg[blockIdx.x], se = a.cta_seg[blockIdx.x + 1];
@@ -643,15 +645,16 @@ __global__ void __launch_bounds__(256) multi_dt_kernel(MultiArgs a, int TX, int 
 #pragma unroll
             for (int q = 0; q < NV; ++q) u[q] = U[(long long)q * N + c];
             double m;
+            R wv[NV];
             if constexpr (MIX) {
-                float wv[NV];
                 mx::recover<ND>(u, mk, wv, flags, floors);
-                m = mx::f2d(mx::cfl_candidate<ND>(u, mk));
+                m = mx::f2d(mx::cfl_from_prim<ND>(wv, mk));
             } else {
-                double wv[NV];
                 recover<ND>(u, g, wv, flags, floors);
                 m = cfl_candidate<ND>(wv, g);
             }
+#pragma unroll
+            for (int q = 0; q < NV; ++q) W[gd->off + (long long)q * N + c] = wv[q];
             wmin = m < wmin ? m : wmin;
         }
         reduce_to_clock<2, 256>(a.clocks + sd.grid, flags, 0u, wmin);
@@ -662,8 +665,9 @@ __global__ void __launch_bounds__(256) multi_dt_kernel(MultiArgs a, int TX, int 
 // the same per-cell candidate as the fused one in stage_kernel<..., 2, ...>.
 // When W is not null it also stores the primitives of U (type R) for the
 // stages that read stored primitives.
+// from_state (mixed / FP32 van Leer): the corrector's estimate from the state.
 template <class R, int ND, class S = double>
-__global__ void __launch_bounds__(256) dt_kernel(Geom g, const double *U, Clock *clk, R *W) {
+__global__ void __launch_bounds__(256) dt_kernel(Geom g, const double *U, Clock *clk, R *W, int from_state) {
     constexpr bool MIX = std::is_same<R, float>::value;
     constexpr bool SINGLE = std::is_same<S, float>::value;
     constexpr int NV = ND + 2;
@@ -679,7 +683,7 @@ __global__ void __launch_bounds__(256) dt_kernel(Geom g, const double *U, Clock 
 #pragma unroll
             for (int q = 0; q < NV; ++q) u[q] = Uf[(long long)q * N + c];
             sg::recover<ND>(u, mk, w, flags, floors);
-            m = (double)sg::cfl_candidate<ND>(u, mk);
+            m = from_state ? mx::f2d(mx::cfl_from_state<ND>(u, mk)) : mx::f2d(mx::cfl_from_prim<ND>(w, mk));
             if (W) {
 #pragma unroll
                 for (int q = 0; q < NV; ++q) W[(long long)q * N + c] = w[q];
@@ -690,7 +694,7 @@ __global__ void __launch_bounds__(256) dt_kernel(Geom g, const double *U, Clock 
             for (int q = 0; q < NV; ++q) u[q] = U[(long long)q * N + c];
             float w[NV];
             mx::recover<ND>(u, mk, w, flags, floors);
-            m = mx::f2d(mx::cfl_candidate<ND>(u, mk));
+            m = from_state ? mx::f2d(mx::cfl_from_state<ND>(u, mk)) : mx::f2d(mx::cfl_from_prim<ND>(w, mk));
             if (W) {
 #pragma unroll
                 for (int q = 0; q < NV; ++q) W[(long long)q * N + c] = w[q];
