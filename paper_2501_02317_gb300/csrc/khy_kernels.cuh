@@ -32,6 +32,11 @@ struct Geom {
     double cfl;
     double rho_floor;
     double p_floor;
+    // the same constants rounded to FP32 on the host (for the FP32 kernels:
+    // read from the parameter bank instead of converted on the device)
+    float f_gamma, f_gm1, f_g1, f_gp1, f_gm1_gp1;
+    float f_rho_floor, f_p_floor;
+    float f_dx[3];
 };
 
 // Device-resident step state.  Written only by clock_kernel (and the host
@@ -169,7 +174,11 @@ struct Consts {
 template <class R>
 __device__ __forceinline__ Consts<R> make_consts(const Geom &g) {
     Consts<R> c;
-    c.gamma = (R)g.gamma; c.gm1 = (R)g.gm1; c.g1 = (R)g.g1; c.gp1 = (R)g.gp1; c.gm1_gp1 = (R)g.gm1_gp1;
+    if constexpr (sizeof(R) == 4) {
+        c.gamma = g.f_gamma; c.gm1 = g.f_gm1; c.g1 = g.f_g1; c.gp1 = g.f_gp1; c.gm1_gp1 = g.f_gm1_gp1;
+    } else {
+        c.gamma = g.gamma; c.gm1 = g.gm1; c.g1 = g.g1; c.gp1 = g.gp1; c.gm1_gp1 = g.gm1_gp1;
+    }
     return c;
 }
 

@@ -111,12 +111,12 @@ struct MixConsts {
 
 __device__ __forceinline__ MixConsts make_mix(const Geom &g) {
     MixConsts k;
-    k.gamma = (float)g.gamma; k.gm1 = (float)g.gm1; k.g1 = (float)g.g1; k.gp1 = (float)g.gp1;
-    k.gm1_gp1 = (float)g.gm1_gp1;
-    k.rho_floor = (float)g.rho_floor; k.p_floor = (float)g.p_floor;
+    k.gamma = g.f_gamma; k.gm1 = g.f_gm1; k.g1 = g.f_g1; k.gp1 = g.f_gp1;
+    k.gm1_gp1 = g.f_gm1_gp1;
+    k.rho_floor = g.f_rho_floor; k.p_floor = g.f_p_floor;
     k.rho_floor_d = g.rho_floor;
     k.rho_floor_bits = __double_as_longlong(g.rho_floor);
-    k.dx[0] = (float)g.dx[0]; k.dx[1] = (float)g.dx[1]; k.dx[2] = (float)g.dx[2];
+    k.dx[0] = g.f_dx[0]; k.dx[1] = g.f_dx[1]; k.dx[2] = g.f_dx[2];
     return k;
 }
 

@@ -214,6 +214,14 @@ Geom make_geom(const khy_mesh_desc &d) {
     g.cfl = d.cfl;
     g.rho_floor = d.rho_floor;
     g.p_floor = d.p_floor;
+    g.f_gamma = (float)g.gamma;
+    g.f_gm1 = (float)g.gm1;
+    g.f_g1 = (float)g.g1;
+    g.f_gp1 = (float)g.gp1;
+    g.f_gm1_gp1 = (float)g.gm1_gp1;
+    g.f_rho_floor = (float)g.rho_floor;
+    g.f_p_floor = (float)g.p_floor;
+    for (int a = 0; a < 3; ++a) g.f_dx[a] = (float)g.dx[a];
     return g;
 }
 
