@@ -88,6 +88,15 @@ struct Tile {
     }
 };
 
+// Asynchronous 4-byte global -> shared copy (no registers, no wait) and the
+// wait for all of this thread's outstanding copies.
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // One segment: tile (x0, y0) of one grid, planes [k0, k1) of its march axis.
 // Shared by the single-grid and the multi-grid kernels.  Accumulates the
 // status bits, the floor count and (stage 2) the CFL minimum into the
@@ -197,6 +206,63 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
         }
     };
 
+    // mixed / FP32 stages that read stored primitives: plane L is copied with
+    // cp.async (issued one plane ahead, while the previous plane's cells are
+    // updated); the ghost-zone velocity rules are applied by the copying
+    // thread after its copies have landed (fix_plane).
+    auto load_plane_async = [&](int L, int slot) {
+        if constexpr (MIX && FROM_W) {
+            R *dst = sW + (size_t)slot * NV * PC;
+            int actm = 0;
+            const int cm = (ND >= 2) ? bc_map(L, g.n[DM], g.bc[DM][0], g.bc[DM][1], &actm) : 0;
+            for (int e = tid; e < PC; e += NT) {
+                const int hx = e % PX, hy = e / PX;
+                if (hx >= wact + 4 || (ND == 3 && hy >= hact + 4)) continue;
+                int act = 0;
+                int c[3] = {0, 0, 0};
+                if (x_inside) c[0] = x0 - 2 + hx;
+                else c[0] = bc_map(x0 - 2 + hx, g.n[0], g.bc[0][0], g.bc[0][1], &act);
+                if (ND == 3) {
+                    if (y_inside) c[1] = y0 - 2 + hy;
+                    else c[1] = bc_map(y0 - 2 + hy, g.n[1], g.bc[1][0], g.bc[1][1], &act);
+                    c[2] = cm;
+                } else if (ND == 2) {
+                    c[1] = cm;
+                }
+                const long long idx = ((long long)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) cp_async4(dst + (size_t)q * PC + e, Win + (long long)q * N + idx);
+            }
+        }
+    };
+    const bool x_rules = !x_inside && (g.bc[0][0] != BC_PERIODIC || g.bc[0][1] != BC_PERIODIC);
+    const bool y_rules = ND == 3 && !y_inside && (g.bc[1][0] != BC_PERIODIC || g.bc[1][1] != BC_PERIODIC);
+    auto fix_plane = [&](int L, int slot) {
+        if constexpr (MIX && FROM_W) {
+            int actm = 0;
+            if (ND >= 2) bc_map(L, g.n[DM], g.bc[DM][0], g.bc[DM][1], &actm);
+            if (!x_rules && !y_rules && actm == 0) return;  // no ghost cell with a velocity rule
+            R *dst = sW + (size_t)slot * NV * PC;
+            for (int e = tid; e < PC; e += NT) {
+                const int hx = e % PX, hy = e / PX;
+                if (hx >= wact + 4 || (ND == 3 && hy >= hact + 4)) continue;
+                int act[3] = {0, 0, 0};
+                if (x_rules) bc_map(x0 - 2 + hx, g.n[0], g.bc[0][0], g.bc[0][1], &act[0]);
+                if (y_rules) bc_map(y0 - 2 + hy, g.n[1], g.bc[1][0], g.bc[1][1], &act[1]);
+                act[DM] = actm;
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {  // ghost-zone velocity rules (Sec. 3.1.1)
+                    if (act[d] == 0) continue;
+                    R v = dst[(size_t)(1 + d) * PC + e];
+                    if (act[d] == 1) v = -v;
+                    else if (act[d] == 2) v = v > R(0) ? R(0) : v;
+                    else v = v < R(0) ? R(0) : v;
+                    dst[(size_t)(1 + d) * PC + e] = v;
+                }
+            }
+        }
+    };
+
     auto gather = [&](const R *base, int e0, int stride, R (&s)[4][NV]) {
 #pragma unroll
         for (int o = 0; o < 4; ++o)
@@ -257,11 +323,18 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
         const float *plane = cp + (size_t)(cur & 3) * NV * PC;
         const int ntask = inplane ? Y_END : M_END;
         for (int k = tid; k < ntask; k += NT) {
-            float2 st[4][NV], Fr[NV];
+            // gather: direction-specific, rotations fixed at compile time;
+            // then one flux call site (keeps the kernel's code small)
+            float2 st[4][NV];
+            int kind, a0, a1;  // 0 march (column col), 1 x (row ty, face p2), 2 y (column tx, face p2)
+            bool vy = true;
             if (k < M_END) {  // march faces between planes cur and cur + 1 of columns 2c, 2c + 1
                 if (k >= NMP) continue;
                 const int col = 2 * k, ctx = col % TX, cty = col / TX;
                 if (ctx >= wact || cty >= hact) continue;
+                kind = 0;
+                a0 = col;
+                a1 = 0;
                 const int e = ((ND == 3) ? (cty + 2) * PX : 0) + ctx + 2;
 #pragma unroll
                 for (int o = 0; o < 4; ++o) {
@@ -270,41 +343,36 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                     for (int j = 0; j < NV; ++j)
                         st[o][j] = *reinterpret_cast<const float2 *>(pl + (size_t)pk::rot_slot<ND>(DM, j) * PC);
                 }
-                pk::face_flux2<ND, PLM>(st, kc_f, Fr);
-#pragma unroll
-                for (int j = 0; j < NV; ++j)
-                    *reinterpret_cast<float2 *>(fm + (size_t)pk::rot_slot<ND>(DM, j) * NT + col) = Fr[j];
             } else if (k < X_END) {  // x faces 2p, 2p + 1 of row ty: cells 2p .. 2p + 4
                 const int x = k - M_END;
                 if (x >= XPR * TY_) continue;
                 const int ty_ = x / XPR, p2 = 2 * (x % XPR);
                 if (p2 > wact || ty_ >= hact) continue;
-                const bool vy = p2 + 1 <= wact;
+                kind = 1;
+                a0 = ty_;
+                a1 = p2;
+                vy = p2 + 1 <= wact;
                 const float *pl = plane + ((ND == 3) ? (ty_ + 2) * PX : 0) + p2;
 #pragma unroll
                 for (int j = 0; j < NV; ++j) {
                     const float *c = pl + (size_t)j * PC;  // rotation onto x is the identity
-                    const float2 a = *reinterpret_cast<const float2 *>(c);
-                    const float2 b = *reinterpret_cast<const float2 *>(c + 2);
-                    const float2 d = *reinterpret_cast<const float2 *>(c + 4);
-                    st[0][j] = a;
-                    st[1][j] = make_float2(a.y, b.x);
-                    st[2][j] = b;
-                    st[3][j] = make_float2(b.y, d.x);
-                }
-                pk::face_flux2<ND, PLM>(st, kc_f, Fr);
-                float *dst = fxo + ty_ * (TX + 1) + p2;
-#pragma unroll
-                for (int j = 0; j < NV; ++j) {
-                    dst[(size_t)j * T::NXF] = Fr[j].x;
-                    if (vy) dst[(size_t)j * T::NXF + 1] = Fr[j].y;
+                    const float2 va = *reinterpret_cast<const float2 *>(c);
+                    const float2 vb = *reinterpret_cast<const float2 *>(c + 2);
+                    const float2 vd = *reinterpret_cast<const float2 *>(c + 4);
+                    st[0][j] = va;
+                    st[1][j] = make_float2(va.y, vb.x);
+                    st[2][j] = vb;
+                    st[3][j] = make_float2(vb.y, vd.x);
                 }
             } else {  // y faces 2p, 2p + 1 of column tx: rows 2p .. 2p + 4
                 const int y = k - X_END;
                 if (y >= YPC * TX) continue;
                 const int tx_ = y % TX, p2 = 2 * (y / TX);
                 if (tx_ >= wact || p2 > hact) continue;
-                const bool vy = p2 + 1 <= hact;
+                kind = 2;
+                a0 = tx_;
+                a1 = p2;
+                vy = p2 + 1 <= hact;
                 const float *pl = plane + p2 * PX + tx_ + 2;
 #pragma unroll
                 for (int j = 0; j < NV; ++j) {
@@ -315,8 +383,22 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                     st[2][j] = make_float2(r2, r3);
                     st[3][j] = make_float2(r3, r4);
                 }
-                pk::face_flux2<ND, PLM>(st, kc_f, Fr);
-                float *dst = fyo + p2 * TX + tx_;
+            }
+            float2 Fr[NV];
+            pk::face_flux2<ND, PLM>(st, kc_f, Fr);
+            if (kind == 0) {
+#pragma unroll
+                for (int j = 0; j < NV; ++j)
+                    *reinterpret_cast<float2 *>(fm + (size_t)pk::rot_slot<ND>(DM, j) * NT + a0) = Fr[j];
+            } else if (kind == 1) {
+                float *dst = fxo + a0 * (TX + 1) + a1;
+#pragma unroll
+                for (int j = 0; j < NV; ++j) {
+                    dst[(size_t)j * T::NXF] = Fr[j].x;
+                    if (vy) dst[(size_t)j * T::NXF + 1] = Fr[j].y;
+                }
+            } else {
+                float *dst = fyo + a1 * TX + a0;
 #pragma unroll
                 for (int j = 0; j < NV; ++j) {
                     dst[(size_t)pk::rot_slot<ND>(1, j) * T::NYF] = Fr[j].x;
@@ -330,13 +412,28 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     // 1, 3, 4, 5 add dt L (or dt/2 L) to a state, stages 2, 6 take the Heun
     // average; then the new state's primitives (stages 3, 5, 6) and its CFL
     // candidate (last stage of a step).
-    auto update_cell = [&](int cur, const R (&Fmlo)[NV], const R (&Fmhi)[NV]) {
+    // the cell's state values (the state this stage adds to, and Un for the
+    // Heun average), loaded ahead of the barrier that precedes the update
+    auto prefetch_cell = [&](int cur, S (&uc)[NV], S (&ub)[NV]) {
         const int gx = x0 + tx;
         const int gy = (ND == 3) ? y0 + ty : (ND == 2 ? cur : 0);
         const int gz = (ND == 3) ? cur : 0;
         if (gx >= g.n[0] || (ND == 3 && gy >= g.n[1])) return;
         const long long idx = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
-        const S *Ucell = (STAGE == 4) ? Ubase : Uin;  // the state this stage adds to
+        const S *Ucell = (STAGE == 4) ? Ubase : Uin;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            uc[q] = Ucell[(long long)q * N + idx];
+            ub[q] = HEUN2 ? Ubase[(long long)q * N + idx] : S(0);
+        }
+    };
+
+    auto update_cell = [&](int cur, const R (&Fmlo)[NV], const R (&Fmhi)[NV], const S (&uc)[NV], const S (&ub)[NV]) {
+        const int gx = x0 + tx;
+        const int gy = (ND == 3) ? y0 + ty : (ND == 2 ? cur : 0);
+        const int gz = (ND == 3) ? cur : 0;
+        if (gx >= g.n[0] || (ND == 3 && gy >= g.n[1])) return;
+        const long long idx = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
         S un[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
@@ -347,19 +444,19 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 float acc = __fmul_rn(c32x, __fsub_rn(fx[0], fx[1]));
                 if (ND == 3) acc = __fmaf_rn(c32y, __fsub_rn(fy[0], fy[TX]), acc);
                 if (ND >= 2) acc = __fmaf_rn(c32m, __fsub_rn((float)Fmlo[q], (float)Fmhi[q]), acc);
-                const float u = Ucell[(long long)q * N + idx];
+                const float u = uc[q];
                 if (!HEUN2) r = __fadd_rn(u, acc);
-                else r = __fmul_rn(0.5f, __fadd_rn(Ubase[(long long)q * N + idx], __fadd_rn(u, acc)));
+                else r = __fmul_rn(0.5f, __fadd_rn(ub[q], __fadd_rn(u, acc)));
             } else if constexpr (!MIX) {
-                const double u = Ucell[(long long)q * N + idx];
+                const double u = uc[q];
                 // dU = -sum_d (dt/dx_d)(F_hi - F_lo), directions in x, y, z order
                 double acc = 0.0 - dtq[0] * (fx[1] - fx[0]);
                 if (ND == 3) acc = acc - dtq[1] * (fy[TX] - fy[0]);
                 if (ND >= 2) acc = acc - dtq[DM] * (Fmhi[q] - Fmlo[q]);
                 if (!HEUN2) r = u + acc;
-                else r = 0.5 * (Ubase[(long long)q * N + idx] + (u + acc));
+                else r = 0.5 * (ub[q] + (u + acc));
             } else {
-                const double u = Ucell[(long long)q * N + idx];
+                const double u = uc[q];
                 // F_lo - F_hi per direction, exact as float-float pairs
                 const mx::FF Dx = mx::two_sum(fx[0], -fx[1]);
                 mx::FF Dy = {0.f, 0.f}, Dm = {0.f, 0.f};
@@ -374,7 +471,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                         r = __fma_rn(dtq[0], mx::f2d_fast(Fs.hi), __dadd_rn(u, lo));
                     } else {
                         const double lo = mx::f2d_fast(__fmul_rn(hc32, Fs.lo));
-                        const double A = __dadd_rn(Ubase[(long long)q * N + idx], u);
+                        const double A = __dadd_rn(ub[q], u);
                         r = __fma_rn(hcd, mx::f2d_fast(Fs.hi), __fma_rn(0.5, A, lo));
                     }
                 } else {
@@ -382,7 +479,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                     if (ND == 3) acc = __fma_rn(dtq[1], mx::f2d_fast(Dy.hi), __fma_rn(dtq[1], mx::f2d_fast(Dy.lo), acc));
                     if (ND >= 2) acc = __fma_rn(dtq[DM], mx::f2d_fast(Dm.hi), __fma_rn(dtq[DM], mx::f2d_fast(Dm.lo), acc));
                     if (!HEUN2) r = __dadd_rn(u, acc);
-                    else r = __dmul_rn(0.5, __dadd_rn(Ubase[(long long)q * N + idx], __dadd_rn(u, acc)));
+                    else r = __dmul_rn(0.5, __dadd_rn(ub[q], __dadd_rn(u, acc)));
                 }
             }
             un[q] = r;
@@ -419,8 +516,39 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
         else inplane_faces(0);
         __syncthreads();
         R dummy[NV];
-        update_cell(0, dummy, dummy);
+        S uc[NV], ub[NV];
+        prefetch_cell(0, uc, ub);
+        update_cell(0, dummy, dummy, uc, ub);
         __syncthreads();
+    } else if constexpr (MIX && FROM_W) {
+        // planes arrive by cp.async one plane ahead; the cell's state values
+        // are loaded before the barrier that precedes its update
+        const bool own = tx < wact && ty < hact;
+        S uc[NV], ub[NV];
+        for (int L = k0 - 2; L <= k0 + 1; ++L) load_plane_async(L, L & 3);
+        for (int L = k0 + 1; L <= k1 + 1; ++L) {
+            cp_async_wait_all();
+            if (L == k0 + 1) {
+                for (int Lp = k0 - 2; Lp <= k0 + 1; ++Lp) fix_plane(Lp, Lp & 3);
+            } else {
+                fix_plane(L, L & 3);
+            }
+            __syncthreads();
+            const int cur = L - 2;
+            faces_mix(cur, cur >= k0);
+            if (cur >= k0 && own) prefetch_cell(cur, uc, ub);
+            __syncthreads();
+            if (L + 1 <= k1 + 1) load_plane_async(L + 1, (L + 1) & 3);  // slot of plane cur - 1, now free
+            if (cur >= k0 && own) {
+                R Fmlo[NV], Fmhi[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    Fmlo[q] = sFm[(size_t)((cur - 1) & 1) * NV * NT + (size_t)q * NT + tid];
+                    Fmhi[q] = sFm[(size_t)(cur & 1) * NV * NT + (size_t)q * NT + tid];
+                }
+                update_cell(cur, Fmlo, Fmhi, uc, ub);
+            }
+        }
     } else if constexpr (MIX) {
         for (int L = k0 - 2; L <= k1 + 1; ++L) {
             load_plane(L, L & 3);
@@ -436,7 +564,9 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                         Fmlo[q] = sFm[(size_t)((cur - 1) & 1) * NV * NT + (size_t)q * NT + tid];
                         Fmhi[q] = sFm[(size_t)(cur & 1) * NV * NT + (size_t)q * NT + tid];
                     }
-                    update_cell(cur, Fmlo, Fmhi);
+                    S uc[NV], ub[NV];
+                    prefetch_cell(cur, uc, ub);
+                    update_cell(cur, Fmlo, Fmhi, uc, ub);
                 }
             } else {
                 __syncthreads();
@@ -464,7 +594,11 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 }
                 if (cur >= k0) inplane_faces(cur & 3);
                 __syncthreads();
-                if (cur >= k0) update_cell(cur, Fmlo, Fmhi);
+                if (cur >= k0) {
+                    S uc[NV], ub[NV];
+                    prefetch_cell(cur, uc, ub);
+                    update_cell(cur, Fmlo, Fmhi, uc, ub);
+                }
 #pragma unroll
                 for (int q = 0; q < NV; ++q) Fmlo[q] = Fmhi[q];
             } else {
