@@ -412,8 +412,11 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     // 1, 3, 4, 5 add dt L (or dt/2 L) to a state, stages 2, 6 take the Heun
     // average; then the new state's primitives (stages 3, 5, 6) and its CFL
     // candidate (last stage of a step).
-    // the cell's state values (the state this stage adds to, and Un for the
-    // Heun average), loaded ahead of the barrier that precedes the update
+    // the cell's state values, loaded ahead of the barrier that precedes the
+    // update: uc = the state this stage adds to; for the Heun average, ub = Un
+    // (all-FP64: kept apart for the reference operation order) or, mixed and
+    // FP32, uc = Un + U1 already summed (fewer live registers)
+    constexpr bool SUM_A = MIX && HEUN2;
     auto prefetch_cell = [&](int cur, S (&uc)[NV], S (&ub)[NV]) {
         const int gx = x0 + tx;
         const int gy = (ND == 3) ? y0 + ty : (ND == 2 ? cur : 0);
@@ -423,8 +426,15 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
         const S *Ucell = (STAGE == 4) ? Ubase : Uin;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-            uc[q] = Ucell[(long long)q * N + idx];
-            ub[q] = HEUN2 ? Ubase[(long long)q * N + idx] : S(0);
+            const S u = Ucell[(long long)q * N + idx];
+            if constexpr (SUM_A) {
+                const S b = Ubase[(long long)q * N + idx];
+                if constexpr (SINGLE) uc[q] = __fadd_rn(b, u);
+                else uc[q] = __dadd_rn(b, u);
+            } else {
+                uc[q] = u;
+                if constexpr (HEUN2) ub[q] = Ubase[(long long)q * N + idx];
+            }
         }
     };
 
@@ -444,9 +454,8 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 float acc = __fmul_rn(c32x, __fsub_rn(fx[0], fx[1]));
                 if (ND == 3) acc = __fmaf_rn(c32y, __fsub_rn(fy[0], fy[TX]), acc);
                 if (ND >= 2) acc = __fmaf_rn(c32m, __fsub_rn((float)Fmlo[q], (float)Fmhi[q]), acc);
-                const float u = uc[q];
-                if (!HEUN2) r = __fadd_rn(u, acc);
-                else r = __fmul_rn(0.5f, __fadd_rn(ub[q], __fadd_rn(u, acc)));
+                if (!HEUN2) r = __fadd_rn(uc[q], acc);
+                else r = __fmaf_rn(0.5f, uc[q], __fmul_rn(0.5f, acc));  // uc = Un + U1
             } else if constexpr (!MIX) {
                 const double u = uc[q];
                 // dU = -sum_d (dt/dx_d)(F_hi - F_lo), directions in x, y, z order
@@ -469,17 +478,16 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                     if (!HEUN2) {
                         const double lo = mx::f2d_fast(__fmul_rn(c32, Fs.lo));
                         r = __fma_rn(dtq[0], mx::f2d_fast(Fs.hi), __dadd_rn(u, lo));
-                    } else {
+                    } else {  // u = Un + U1
                         const double lo = mx::f2d_fast(__fmul_rn(hc32, Fs.lo));
-                        const double A = __dadd_rn(ub[q], u);
-                        r = __fma_rn(hcd, mx::f2d_fast(Fs.hi), __fma_rn(0.5, A, lo));
+                        r = __fma_rn(hcd, mx::f2d_fast(Fs.hi), __fma_rn(0.5, u, lo));
                     }
                 } else {
                     double acc = __fma_rn(dtq[0], mx::f2d_fast(Dx.hi), __dmul_rn(dtq[0], mx::f2d_fast(Dx.lo)));
                     if (ND == 3) acc = __fma_rn(dtq[1], mx::f2d_fast(Dy.hi), __fma_rn(dtq[1], mx::f2d_fast(Dy.lo), acc));
                     if (ND >= 2) acc = __fma_rn(dtq[DM], mx::f2d_fast(Dm.hi), __fma_rn(dtq[DM], mx::f2d_fast(Dm.lo), acc));
                     if (!HEUN2) r = __dadd_rn(u, acc);
-                    else r = __dmul_rn(0.5, __dadd_rn(ub[q], __dadd_rn(u, acc)));
+                    else r = __fma_rn(0.5, u, __dmul_rn(0.5, acc));  // u = Un + U1
                 }
             }
             un[q] = r;
