@@ -194,14 +194,28 @@ __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ double rroot(double a) { return __dsqrt_rn(a); }
 // FP32 (mixed path): division and square root use the special-function
-// unit's approximations (a few ulp, far inside the mixed path's tolerance);
-// they are still pure functions of their inputs, so redundant face fluxes
-// stay bitwise identical.
+// unit's approximate reciprocal (max error 1 ulp) and reciprocal square root
+// (relative error below 2^-22.9), one instruction each, with subnormals
+// flushed (PTX rcp.approx.ftz / rsqrt.approx.ftz); far inside the mixed
+// path's tolerance, and still pure functions of their inputs, so redundant
+// face fluxes stay bitwise identical.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float rdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ float rroot(float a) { return a > 0.f ? __fmul_rn(a, rsqrtf(a)) : 0.f; }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fmul_rn(a, rcp_approx(b)); }
+__device__ __forceinline__ float rroot(float a) { return a > 0.f ? __fmul_rn(a, rsqrt_approx(a)) : 0.f; }
+// square root of an argument known to be >= 1 (no zero guard)
+__device__ __forceinline__ float rroot_ge1(float a) { return __fmul_rn(a, rsqrt_approx(a)); }
 
 // ------------------------------------------------------------ Sec. 3.2.2
 // HLLC flux for rotated primitive states w = (rho, u, t_1..t_NT, p), NT

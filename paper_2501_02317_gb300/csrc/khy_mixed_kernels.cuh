@@ -143,7 +143,7 @@ __device__ __forceinline__ void recover(const double (&u)[ND + 2], const MixCons
         ++floors;
     }
     const float rho32 = d2f(rho);
-    const float r32 = __fdividef(1.0f, rho32);  // ~1 ulp; the FP64 Newton step below squares its error
+    const float r32 = rcp_approx(rho32);  // ~1 ulp; the FP64 Newton step below squares its error
     double r = f2d_fast(r32);
     const double e = __fma_rn(-rho, r, 1.0);  // one Newton step: |1 - rho r| ~ 2^-46
     r = __fma_rn(r, e, r);
@@ -190,7 +190,7 @@ template <int ND, class S>
 __device__ __forceinline__ float cfl_from_state(const S (&u)[ND + 2], const MixConsts &k) {
     float rho = abs_d2f_rz(u[0]);
     if (!(rho >= k.rho_floor)) rho = k.rho_floor;
-    const float r = __fdividef(1.0f, rho);
+    const float r = rcp_approx(rho);
     float v[ND];
     float vsq = 0.f;
 #pragma unroll

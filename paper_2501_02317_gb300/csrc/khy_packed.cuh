@@ -20,8 +20,19 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 div2(float2 a, float2 b) { return make_float2(rdiv(a.x, b.x), rdiv(a.y, b.y)); }
-__device__ __forceinline__ float2 root2(float2 a) { return make_float2(rroot(a.x), rroot(a.y)); }
+// a / b: two special-function reciprocals, one packed multiply
+__device__ __forceinline__ float2 div2(float2 a, float2 b) {
+    return __fmul2_rn(a, make_float2(rcp_approx(b.x), rcp_approx(b.y)));
+}
+// sqrt(a), 0 for a <= 0: two reciprocal square roots, one packed multiply
+__device__ __forceinline__ float2 root2(float2 a) {
+    const float2 r = __fmul2_rn(a, make_float2(rsqrt_approx(a.x), rsqrt_approx(a.y)));
+    return make_float2(a.x > 0.f ? r.x : 0.f, a.y > 0.f ? r.y : 0.f);
+}
+// sqrt(a) for a >= 1
+__device__ __forceinline__ float2 root2_ge1(float2 a) {
+    return __fmul2_rn(a, make_float2(rsqrt_approx(a.x), rsqrt_approx(a.y)));
+}
 __device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
     return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
@@ -29,10 +40,9 @@ __device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
 __device__ __forceinline__ float2 max2(float2 a, float2 b) { return make_float2(a.x > b.x ? a.x : b.x, a.y > b.y ? a.y : b.y); }
 
 // minmod (Eq. 3): the smaller magnitude with the common sign, 0 if the signs
-// differ (or either is 0): min(|a|, |b|) carries the sign of a.
+// differ (or either is 0) -- the median of (0, a, b), four min/max operations.
 __device__ __forceinline__ float minmod1(float a, float b) {
-    const float m = copysignf(fminf(fabsf(a), fabsf(b)), a);
-    return (__float_as_int(a) ^ __float_as_int(b)) >= 0 ? m : 0.f;
+    return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.f));
 }
 __device__ __forceinline__ float2 minmod2(float2 a, float2 b) { return make_float2(minmod1(a.x, b.x), minmod1(a.y, b.y)); }
 
@@ -63,8 +73,8 @@ __device__ __forceinline__ void hllc2(const Consts<float> &k, const float2 (&wl)
     const float2 one = splat(1.f);
     const float2 ratl = max2(div2(pstar, pl), one);
     const float2 ratr = max2(div2(pstar, pr), one);
-    const float2 ql = root2(fma2(splat(k.g1), sub2(ratl, one), one));
-    const float2 qr = root2(fma2(splat(k.g1), sub2(ratr, one), one));
+    const float2 ql = root2_ge1(fma2(splat(k.g1), sub2(ratl, one), one));  // rat >= 1
+    const float2 qr = root2_ge1(fma2(splat(k.g1), sub2(ratr, one), one));
     const float2 dsl = mul2(splat(-1.f), mul2(cl, ql));
     const float2 dsr = mul2(cr, qr);
     const float2 sl = add2(ul, dsl);

@@ -22,7 +22,7 @@ __device__ __forceinline__ void recover(const float (&u)[ND + 2], const mx::MixC
         flags |= FLAG_FLOOR;
         ++floors;
     }
-    const float r = __frcp_rn(rho);
+    const float r = rcp_approx(rho);
     float msq = __fmul_rn(u[1], u[1]);
 #pragma unroll
     for (int d = 1; d < ND; ++d) msq = __fmaf_rn(u[1 + d], u[1 + d], msq);
