@@ -34,7 +34,7 @@ struct Geom {
     double p_floor;
     // the same constants rounded to FP32 on the host (for the FP32 kernels:
     // read from the parameter bank instead of converted on the device)
-    float f_gamma, f_gm1, f_g1, f_gp1, f_gm1_gp1;
+    float f_gamma, f_gm1, f_g1, f_gp1, f_gm1_gp1, f_igm1;  // f_igm1 = 1 / (gamma - 1)
     float f_rho_floor, f_p_floor;
     float f_dx[3];
 };
@@ -169,6 +169,7 @@ __device__ __forceinline__ R minmod(R a, R b) {
 template <class R>
 struct Consts {
     R gamma, gm1, g1, gp1, gm1_gp1;
+    R igm1;  // 1 / (gamma - 1), FP32 path only
 };
 
 template <class R>
@@ -176,8 +177,10 @@ __device__ __forceinline__ Consts<R> make_consts(const Geom &g) {
     Consts<R> c;
     if constexpr (sizeof(R) == 4) {
         c.gamma = g.f_gamma; c.gm1 = g.f_gm1; c.g1 = g.f_g1; c.gp1 = g.f_gp1; c.gm1_gp1 = g.f_gm1_gp1;
+        c.igm1 = g.f_igm1;
     } else {
         c.gamma = g.gamma; c.gm1 = g.gm1; c.g1 = g.g1; c.gp1 = g.gp1; c.gm1_gp1 = g.gm1_gp1;
+        c.igm1 = 0.0;  // the FP64 flux divides by gamma - 1, as the reference does
     }
     return c;
 }

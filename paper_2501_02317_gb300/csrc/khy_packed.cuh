@@ -55,9 +55,15 @@ __device__ __forceinline__ void hllc2(const Consts<float> &k, const float2 (&wl)
     constexpr int P = NT + 2;
     const float2 rl = wl[0], ul = wl[1], pl = wl[P];
     const float2 rr = wr[0], ur = wr[1], pr = wr[P];
+    // c = sqrt(gamma p / rho) = a rsqrt(a rho) with a = gamma p: one
+    // special-function operation per lane; 0 where a = 0
     const float2 g = splat(k.gamma);
-    const float2 cl = root2(div2(mul2(g, pl), rl));
-    const float2 cr = root2(div2(mul2(g, pr), rr));
+    const float2 al = mul2(g, pl), ar = mul2(g, pr);
+    const float2 xl = mul2(al, rl), xr = mul2(ar, rr);
+    float2 cl = mul2(al, make_float2(rsqrt_approx(xl.x), rsqrt_approx(xl.y)));
+    float2 cr = mul2(ar, make_float2(rsqrt_approx(xr.x), rsqrt_approx(xr.y)));
+    cl = make_float2(xl.x > 0.f ? cl.x : 0.f, xl.y > 0.f ? cl.y : 0.f);
+    cr = make_float2(xr.x > 0.f ? cr.x : 0.f, xr.y > 0.f ? cr.y : 0.f);
     const float2 du = sub2(ur, ul);
     const float2 ppv = sub2(mul2(splat(0.5f), add2(pl, pr)), mul2(mul2(mul2(splat(0.125f), du), add2(rl, rr)), add2(cl, cr)));
     float2 pstar = max2(ppv, splat(0.f));
@@ -93,7 +99,7 @@ __device__ __forceinline__ void hllc2(const Consts<float> &k, const float2 (&wl)
     float2 vsq = mul2(uk, uk);
 #pragma unroll
     for (int j = 0; j < NT; ++j) vsq = fma2(w[2 + j], w[2 + j], vsq);
-    const float2 E = fma2(mul2(splat(0.5f), rk), vsq, div2(pk, splat(k.gm1)));
+    const float2 E = fma2(mul2(splat(0.5f), rk), vsq, mul2(pk, splat(k.igm1)));
     const float2 mf = mul2(rk, uk);
     float2 Uk[NT + 3], Fk[NT + 3];
     Uk[0] = rk;

@@ -219,6 +219,7 @@ Geom make_geom(const khy_mesh_desc &d) {
     g.f_g1 = (float)g.g1;
     g.f_gp1 = (float)g.gp1;
     g.f_gm1_gp1 = (float)g.gm1_gp1;
+    g.f_igm1 = (float)(1.0 / g.gm1);
     g.f_rho_floor = (float)g.rho_floor;
     g.f_p_floor = (float)g.p_floor;
     for (int a = 0; a < 3; ++a) g.f_dx[a] = (float)g.dx[a];

@@ -299,21 +299,21 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     // warps, so a warp always works on one direction and every rotation is a
     // compile-time constant.  A task computes two neighbouring faces of one
     // direction as the two lanes of the packed face_flux2, from one shared
-    // stencil: x and y faces f, f+1 of one row or column share a five-cell
-    // stencil; march faces of the column pair (2c, 2c+1) are read as float2
-    // pairs from the four ring planes.  March fluxes go to sFm[cur & 1],
+    // stencil: x faces f, f+1 of one row share a five-cell stencil (three
+    // float2 loads); y faces and march faces of the column pair (2c, 2c+1)
+    // are read as float2 pairs (along y within the plane, along the march
+    // axis from the four ring planes).  March fluxes go to sFm[cur & 1],
     // in-plane ones to sFx / sFy.  The last pair of an x row (faces TX, TX+1)
-    // and of a y column (TY, TY+1) has one valid lane; its idle lane reads
-    // shared memory past the row (other fields or the flux buffers) and
-    // stores nothing.
+    // has one valid lane; its idle lane reads shared memory past the row
+    // (other fields or the flux buffers) and stores nothing.
     R *sFm = sFy + (size_t)NV * T::NYF;  // [2][NV][NT], mixed path only
     constexpr int XPR = (TX + 2) / 2;                  // x-face pairs per row (faces 0..TX)
-    constexpr int YPC = (ND == 3) ? (TY + 2) / 2 : 0;  // y-face pairs per column (faces 0..TY)
+    constexpr int YPC = (ND == 3) ? TY + 1 : 0;        // y faces per column pair (faces 0..TY)
     constexpr int TY_ = (ND == 3) ? TY : 1;
     constexpr int NMP = (ND >= 2) ? NT / 2 : 0;        // march-face column pairs
     constexpr int M_END = (NMP + 31) / 32 * 32;
     constexpr int X_END = M_END + (XPR * TY_ + 31) / 32 * 32;
-    constexpr int Y_END = X_END + (YPC * TX + 31) / 32 * 32;
+    constexpr int Y_END = X_END + (YPC * (TX / 2) + 31) / 32 * 32;
     static_assert(TX % 2 == 0 && (ND != 3 || TY % 2 == 0), "face pairs need even tile sides");
     auto faces_mix = [&](int cur, bool inplane) {
         const float *cp = reinterpret_cast<const float *>(sW);
@@ -326,7 +326,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
             // gather: direction-specific, rotations fixed at compile time;
             // then one flux call site (keeps the kernel's code small)
             float2 st[4][NV];
-            int kind, a0, a1;  // 0 march (column col), 1 x (row ty, face p2), 2 y (column tx, face p2)
+            int kind, a0, a1;  // 0 march (column col), 1 x (row ty, face p2), 2 y (column tx, face fy)
             bool vy = true;
             if (k < M_END) {  // march faces between planes cur and cur + 1 of columns 2c, 2c + 1
                 if (k >= NMP) continue;
@@ -364,25 +364,20 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                     st[2][j] = vb;
                     st[3][j] = make_float2(vb.y, vd.x);
                 }
-            } else {  // y faces 2p, 2p + 1 of column tx: rows 2p .. 2p + 4
+            } else {  // y face fy of columns 2c, 2c + 1: rows fy .. fy + 3
                 const int y = k - X_END;
-                if (y >= YPC * TX) continue;
-                const int tx_ = y % TX, p2 = 2 * (y / TX);
-                if (tx_ >= wact || p2 > hact) continue;
+                if (y >= YPC * (TX / 2)) continue;
+                const int tx_ = 2 * (y % (TX / 2)), fy = y / (TX / 2);
+                if (tx_ >= wact || fy > hact) continue;
                 kind = 2;
                 a0 = tx_;
-                a1 = p2;
-                vy = p2 + 1 <= hact;
-                const float *pl = plane + p2 * PX + tx_ + 2;
+                a1 = fy;
+                const float *pl = plane + fy * PX + tx_ + 2;
 #pragma unroll
-                for (int j = 0; j < NV; ++j) {
-                    const float *c = pl + (size_t)pk::rot_slot<ND>(1, j) * PC;
-                    const float r0 = c[0], r1 = c[PX], r2 = c[2 * PX], r3 = c[3 * PX], r4 = c[4 * PX];
-                    st[0][j] = make_float2(r0, r1);
-                    st[1][j] = make_float2(r1, r2);
-                    st[2][j] = make_float2(r2, r3);
-                    st[3][j] = make_float2(r3, r4);
-                }
+                for (int o = 0; o < 4; ++o)
+#pragma unroll
+                    for (int j = 0; j < NV; ++j)
+                        st[o][j] = *reinterpret_cast<const float2 *>(pl + (size_t)pk::rot_slot<ND>(1, j) * PC + o * PX);
             }
             float2 Fr[NV];
             pk::face_flux2<ND, PLM>(st, kc_f, Fr);
@@ -400,10 +395,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
             } else {
                 float *dst = fyo + a1 * TX + a0;
 #pragma unroll
-                for (int j = 0; j < NV; ++j) {
-                    dst[(size_t)pk::rot_slot<ND>(1, j) * T::NYF] = Fr[j].x;
-                    if (vy) dst[(size_t)pk::rot_slot<ND>(1, j) * T::NYF + TX] = Fr[j].y;
-                }
+                for (int j = 0; j < NV; ++j) *reinterpret_cast<float2 *>(dst + (size_t)pk::rot_slot<ND>(1, j) * T::NYF) = Fr[j];
             }
         }
     };
