@@ -26,6 +26,19 @@ namespace khy {
 namespace mx {
 
 // ---------------------------------------------------------------- conversions
+// double -> float for the primitives of a finite state: round to nearest
+// (ties away from zero), results below the float normal range flush to zero;
+// |x| must stay below 2^128 (a non-finite or huge state is flagged by the
+// FP64 checks of the recovery).  Seven integer operations.
+__device__ __forceinline__ float d2f_state(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned a = hi & 0x7FFFFFFFu;
+    // exponent re-bias 1023 -> 127 on the high word, then 20 + 3 mantissa bits
+    unsigned f = __funnelshift_l(lo, a - 0x38000000u, 3);
+    f += (lo >> 28) & 1u;  // the first dropped bit rounds (a carry may reach the exponent)
+    return __uint_as_float((a < 0x38100000u ? 0u : f) | (hi & 0x80000000u));
+}
+
 // double -> float, round to nearest even; results below the float normal
 // range flush to zero, above it become +-inf; NaN stays NaN.
 __device__ __forceinline__ float d2f(double x) {
@@ -142,7 +155,7 @@ __device__ __forceinline__ void recover(const double (&u)[ND + 2], const MixCons
         flags |= FLAG_FLOOR;
         ++floors;
     }
-    const float rho32 = d2f(rho);
+    const float rho32 = d2f_state(rho);
     const float r32 = rcp_approx(rho32);  // ~1 ulp; the FP64 Newton step below squares its error
     double r = f2d_fast(r32);
     const double e = __fma_rn(-rho, r, 1.0);  // one Newton step: |1 - rho r| ~ 2^-46
@@ -152,7 +165,7 @@ __device__ __forceinline__ void recover(const double (&u)[ND + 2], const MixCons
     for (int d = 1; d < ND; ++d) msq = __fma_rn(u[1 + d], u[1 + d], msq);
     const double eint = __fma_rn(-0.5, __dmul_rn(msq, r), u[ND + 1]);
     if (negative_or_nan(eint)) flags |= FLAG_NONPHYSICAL;
-    float p = __fmul_rn(k.gm1, d2f(eint));
+    float p = __fmul_rn(k.gm1, d2f_state(eint));
     if (p < k.p_floor) {
         p = k.p_floor;
         flags |= FLAG_FLOOR;
@@ -160,7 +173,7 @@ __device__ __forceinline__ void recover(const double (&u)[ND + 2], const MixCons
     }
     w[0] = rho32;
 #pragma unroll
-    for (int d = 0; d < ND; ++d) w[1 + d] = __fmul_rn(d2f(u[1 + d]), r32);
+    for (int d = 0; d < ND; ++d) w[1 + d] = __fmul_rn(d2f_state(u[1 + d]), r32);
     w[ND + 1] = p;
 }
 
