@@ -128,6 +128,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     const long long N = g.ncell;
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
+    float wmin_f = __int_as_float(0x7F800000);  // FP32 CFL minimum of this segment (mixed / FP32)
     // active extent of this tile (ragged tiles and grids narrower than a tile)
     const int wact = min(TX, g.n[0] - x0);
     const int hact = (ND == 3) ? min(TY, g.n[1] - y0) : 1;
@@ -501,11 +502,15 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
             }
         }
         if (CFL) {  // CFL candidate of the new state for the next step
-            double c;
-            if constexpr (CFL_STATE) c = mx::f2d(mx::cfl_from_state<ND>(un, mk));
-            else if constexpr (MIX) c = mx::f2d(mx::cfl_from_prim<ND>(w, mk));
-            else c = cfl_candidate<ND>(w, g);
-            wmin = c < wmin ? c : wmin;
+            if constexpr (MIX) {  // FP32 minimum (no FP64 compare per cell)
+                float c;
+                if constexpr (CFL_STATE) c = mx::cfl_from_state<ND>(un, mk);
+                else c = mx::cfl_from_prim<ND>(w, mk);
+                wmin_f = c < wmin_f ? c : wmin_f;
+            } else {
+                const double c = cfl_candidate<ND>(w, g);
+                wmin = c < wmin ? c : wmin;
+            }
         }
     };
 
@@ -605,6 +610,10 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 __syncthreads();
             }
         }
+    }
+    if constexpr (MIX) {
+        const double c = mx::f2d(wmin_f);
+        wmin = c < wmin ? c : wmin;
     }
 }
 
