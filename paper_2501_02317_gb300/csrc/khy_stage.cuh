@@ -408,8 +408,15 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     // the cell's state values, loaded ahead of the barrier that precedes the
     // update: uc = the state this stage adds to; for the Heun average, ub = Un
     // (all-FP64: kept apart for the reference operation order) or, mixed and
-    // FP32, uc = Un + U1 already summed (fewer live registers)
-    constexpr bool SUM_A = MIX && HEUN2;
+    // FP32, uc = Un + U1 already summed (fewer live registers).
+    // The all-FP32 stage 5 stores V = (Un + U1) / 2 (exact halving) in place
+    // of U1 -- its primitives are stored as well -- so stage 6 adds to V and
+    // reads no Un: V + acc/2 equals fma(0.5, Un + U1, acc/2) bit for bit.  (In
+    // the mixed path the extra FP64 add in stage 5 costs more than the Un
+    // read it saves in stage 6.)
+    constexpr bool STORE_V = SINGLE && STAGE == 5;
+    constexpr bool FROM_V = SINGLE && STAGE == 6;
+    constexpr bool SUM_A = MIX && HEUN2 && !FROM_V;
     auto prefetch_cell = [&](int cur, S (&uc)[NV], S (&ub)[NV]) {
         const int gx = x0 + tx;
         const int gy = (ND == 3) ? y0 + ty : (ND == 2 ? cur : 0);
@@ -426,7 +433,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 else uc[q] = __dadd_rn(b, u);
             } else {
                 uc[q] = u;
-                if constexpr (HEUN2) ub[q] = Ubase[(long long)q * N + idx];
+                if constexpr (HEUN2 && !FROM_V) ub[q] = Ubase[(long long)q * N + idx];
             }
         }
     };
@@ -448,7 +455,8 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 if (ND == 3) acc = __fmaf_rn(c32y, __fsub_rn(fy[0], fy[TX]), acc);
                 if (ND >= 2) acc = __fmaf_rn(c32m, __fsub_rn((float)Fmlo[q], (float)Fmhi[q]), acc);
                 if (!HEUN2) r = __fadd_rn(uc[q], acc);
-                else r = __fmaf_rn(0.5f, uc[q], __fmul_rn(0.5f, acc));  // uc = Un + U1
+                else if (FROM_V) r = __fadd_rn(uc[q], __fmul_rn(0.5f, acc));  // uc = V
+                else r = __fmaf_rn(0.5f, uc[q], __fmul_rn(0.5f, acc));   // uc = Un + U1
             } else if constexpr (!MIX) {
                 const double u = uc[q];
                 // dU = -sum_d (dt/dx_d)(F_hi - F_lo), directions in x, y, z order
@@ -484,7 +492,11 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 }
             }
             un[q] = r;
-            if (WRITE_U) Uout[(long long)q * N + idx] = r;
+            if constexpr (STORE_V) {
+                Uout[(long long)q * N + idx] = __fmul_rn(0.5f, __fadd_rn(uc[q], r));
+            } else if (WRITE_U) {
+                Uout[(long long)q * N + idx] = r;
+            }
         }
         // CFL estimate of the van Leer corrector (mixed / FP32): straight from
         // the state, which it does not recover
