@@ -81,11 +81,18 @@ struct Tile {
     static constexpr int NYF = (ND == 3) ? TX * (TY + 1) : 0;
     // mixed path: march-axis fluxes of the last two planes also live in shared memory
     static constexpr int NFM = (ND >= 2) ? 2 * NV * NT : 0;
+    // buffer offsets in elements, each a multiple of 4 (16 bytes for FP32): the
+    // FP32 face loop reads and writes float2 pairs at even offsets within them
+    static constexpr int up4(int v) { return (v + 3) / 4 * 4; }
+    static constexpr int OFF_FX = up4(NSLOT * NV * PC);
+    static constexpr int OFF_FY = OFF_FX + up4(NV * NXF);
+    static constexpr int OFF_FM = OFF_FY + up4(NV * NYF);
     template <class R>
     static constexpr size_t smem_bytes() {
-        return sizeof(R) * ((size_t)NSLOT * NV * PC + (size_t)NV * NXF + (size_t)NV * NYF +
-                            (std::is_same<R, float>::value ? (size_t)NFM : 0));
+        return sizeof(R) * ((size_t)OFF_FM + (std::is_same<R, float>::value ? (size_t)NFM : 0));
     }
+    static_assert(PX % 2 == 0 && PC % 2 == 0 && NYF % 2 == 0 && NT % 2 == 0,
+                  "float2 accesses need even row, plane, flux-row and column strides");
 };
 
 // Asynchronous 4-byte global -> shared copy (no registers, no wait) and the
@@ -307,7 +314,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     // in-plane ones to sFx / sFy.  The last pair of an x row (faces TX, TX+1)
     // has one valid lane; its idle lane reads shared memory past the row
     // (other fields or the flux buffers) and stores nothing.
-    R *sFm = sFy + (size_t)NV * T::NYF;  // [2][NV][NT], mixed path only
+    R *sFm = sW + T::OFF_FM;  // [2][NV][NT], mixed path only
     constexpr int XPR = (TX + 2) / 2;                  // x-face pairs per row (faces 0..TX)
     constexpr int YPC = (ND == 3) ? TY + 1 : 0;        // y faces per column pair (faces 0..TY)
     constexpr int TY_ = (ND == 3) ? TY : 1;
@@ -315,7 +322,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     constexpr int M_END = (NMP + 31) / 32 * 32;
     constexpr int X_END = M_END + (XPR * TY_ + 31) / 32 * 32;
     constexpr int Y_END = X_END + (YPC * (TX / 2) + 31) / 32 * 32;
-    static_assert(TX % 2 == 0 && (ND != 3 || TY % 2 == 0), "face pairs need even tile sides");
+    static_assert(TX % 2 == 0, "face pairs need an even tile width");
     auto faces_mix = [&](int cur, bool inplane) {
         const float *cp = reinterpret_cast<const float *>(sW);
         float *fm = reinterpret_cast<float *>(sFm) + (size_t)(cur & 1) * NV * NT;
@@ -681,8 +688,8 @@ __global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) stage_ke
     constexpr int DM = ND - 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sW = reinterpret_cast<R *>(smem_raw);   // [NSLOT][NV][PC] primitives
-    R *sFx = sW + (size_t)T::NSLOT * NV * PC;  // [NV][TY][TX+1] x-face fluxes
-    R *sFy = sFx + (size_t)NV * T::NXF;        // [NV][TY+1][TX] y-face fluxes (3D)
+    R *sFx = sW + T::OFF_FX;  // [NV][TY][TX+1] x-face fluxes
+    R *sFy = sW + T::OFF_FY;  // [NV][TY+1][TX] y-face fluxes (3D)
 
     const Geom &g = a.g;
     const Clock *clk = a.clk;
@@ -750,8 +757,8 @@ __global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) multi_st
     constexpr int NV = T::NV, PC = T::PC, NT = T::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sW = reinterpret_cast<R *>(smem_raw);
-    R *sFx = sW + (size_t)T::NSLOT * NV * PC;
-    R *sFy = sFx + (size_t)NV * T::NXF;
+    R *sFx = sW + T::OFF_FX;
+    R *sFy = sW + T::OFF_FY;
     const int sb = a.cta_seg[blockIdx.x], se = a.cta_seg[blockIdx.x + 1];
     for (int si = sb; si < se; ++si) {
         const SegDesc sd = a.segs[si];
