@@ -39,6 +39,30 @@ __device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 max2(float2 a, float2 b) { return make_float2(a.x > b.x ? a.x : b.x, a.y > b.y ? a.y : b.y); }
 
+// Float-float pairs of two independent sums (lanes): the same round-to-nearest
+// operations as the scalar Knuth TwoSum, so each lane has the scalar's bits.
+struct FF2 {
+    float2 hi, lo;
+};
+__device__ __forceinline__ FF2 two_sum2(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    return {s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+// exact a - b as a float-float pair: TwoSum(a, -b) without the negation
+// (round-to-nearest is symmetric, so the bits are those of TwoSum(a, -b))
+__device__ __forceinline__ FF2 two_diff2(float2 a, float2 b) {
+    const float2 s = sub2(a, b);
+    const float2 bb = sub2(s, a);
+    return {s, sub2(sub2(a, sub2(s, bb)), add2(b, bb))};
+}
+__device__ __forceinline__ FF2 ff_add2(FF2 a, FF2 b) {
+    const FF2 s = two_sum2(a.hi, b.hi);
+    const float2 e = add2(s.lo, add2(a.lo, b.lo));
+    const float2 hi = add2(s.hi, e);
+    return {hi, sub2(e, sub2(hi, s.hi))};
+}
+
 // minmod (Eq. 3): the smaller magnitude with the common sign, 0 if the signs
 // differ (or either is 0) -- the median of (0, a, b), four min/max operations.
 __device__ __forceinline__ float minmod1(float a, float b) {

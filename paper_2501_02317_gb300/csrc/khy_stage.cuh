@@ -451,9 +451,54 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
         const int gz = (ND == 3) ? cur : 0;
         if (gx >= g.n[0] || (ND == 3 && gy >= g.n[1])) return;
         const long long idx = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
+        // mixed, equal dx: the six face fluxes of each field summed exactly as
+        // a float-float pair, two fields per packed operation (lanes), then
+        // the FP64 update of those two fields
         S un[NV];
+        bool packed_done = false;
+        if constexpr (MIX && !SINGLE) {
+            if (cubic) {
+                const float *fxb = reinterpret_cast<const float *>(sFx) + ty * (TX + 1) + tx;
+                const float *fyb = reinterpret_cast<const float *>(sFy) + ty * TX + tx;
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
+                for (int p = 0; p < (NV + 1) / 2; ++p) {
+                    const int q0 = 2 * p, q1 = (2 * p + 1 < NV) ? 2 * p + 1 : 2 * p;
+                    const float2 xl = make_float2(fxb[(size_t)q0 * T::NXF], fxb[(size_t)q1 * T::NXF]);
+                    const float2 xh = make_float2(fxb[(size_t)q0 * T::NXF + 1], fxb[(size_t)q1 * T::NXF + 1]);
+                    pk::FF2 Fs = pk::two_diff2(xl, xh);
+                    if (ND == 3) {
+                        const float2 yl = make_float2(fyb[(size_t)q0 * T::NYF], fyb[(size_t)q1 * T::NYF]);
+                        const float2 yh = make_float2(fyb[(size_t)q0 * T::NYF + TX], fyb[(size_t)q1 * T::NYF + TX]);
+                        Fs = pk::ff_add2(Fs, pk::two_diff2(yl, yh));
+                    }
+                    if (ND >= 2) {
+                        const float2 ml = make_float2((float)Fmlo[q0], (float)Fmlo[q1]);
+                        const float2 mh = make_float2((float)Fmhi[q0], (float)Fmhi[q1]);
+                        Fs = pk::ff_add2(Fs, pk::two_diff2(ml, mh));
+                    }
+#pragma unroll
+                    for (int l = 0; l < 2; ++l) {
+                        const int q = 2 * p + l;
+                        if (q >= NV) break;
+                        const float fhi = l ? Fs.hi.y : Fs.hi.x, flo = l ? Fs.lo.y : Fs.lo.x;
+                        const double u = uc[q];
+                        double r;
+                        if (!HEUN2) {
+                            const double lo = mx::f2d_fast(__fmul_rn(c32, flo));
+                            r = __fma_rn(dtq[0], mx::f2d_fast(fhi), __dadd_rn(u, lo));
+                        } else {  // u = Un + U1
+                            const double lo = mx::f2d_fast(__fmul_rn(hc32, flo));
+                            r = __fma_rn(hcd, mx::f2d_fast(fhi), __fma_rn(0.5, u, lo));
+                        }
+                        un[q] = r;
+                        if (WRITE_U) Uout[(long long)q * N + idx] = r;
+                    }
+                }
+                packed_done = true;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NV && !packed_done; ++q) {
             const R *fx = sFx + (size_t)q * T::NXF + ty * (TX + 1) + tx;
             const R *fy = sFy + (size_t)q * T::NYF + ty * TX + tx;
             S r;
@@ -474,23 +519,12 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 else r = 0.5 * (ub[q] + (u + acc));
             } else {
                 const double u = uc[q];
-                // F_lo - F_hi per direction, exact as float-float pairs
-                const mx::FF Dx = mx::two_sum(fx[0], -fx[1]);
-                mx::FF Dy = {0.f, 0.f}, Dm = {0.f, 0.f};
-                if (ND == 3) Dy = mx::two_sum(fy[0], -fy[TX]);
-                if (ND >= 2) Dm = mx::two_sum(Fmlo[q], -Fmhi[q]);
-                if (cubic) {
-                    mx::FF Fs = Dx;
-                    if (ND == 3) Fs = mx::ff_add(Fs, Dy);
-                    if (ND >= 2) Fs = mx::ff_add(Fs, Dm);
-                    if (!HEUN2) {
-                        const double lo = mx::f2d_fast(__fmul_rn(c32, Fs.lo));
-                        r = __fma_rn(dtq[0], mx::f2d_fast(Fs.hi), __dadd_rn(u, lo));
-                    } else {  // u = Un + U1
-                        const double lo = mx::f2d_fast(__fmul_rn(hc32, Fs.lo));
-                        r = __fma_rn(hcd, mx::f2d_fast(Fs.hi), __fma_rn(0.5, u, lo));
-                    }
-                } else {
+                {  // unequal dx (equal dx is the packed path above)
+                    // F_lo - F_hi per direction, exact as float-float pairs
+                    const mx::FF Dx = mx::two_sum(fx[0], -fx[1]);
+                    mx::FF Dy = {0.f, 0.f}, Dm = {0.f, 0.f};
+                    if (ND == 3) Dy = mx::two_sum(fy[0], -fy[TX]);
+                    if (ND >= 2) Dm = mx::two_sum(Fmlo[q], -Fmhi[q]);
                     double acc = __fma_rn(dtq[0], mx::f2d_fast(Dx.hi), __dmul_rn(dtq[0], mx::f2d_fast(Dx.lo)));
                     if (ND == 3) acc = __fma_rn(dtq[1], mx::f2d_fast(Dy.hi), __fma_rn(dtq[1], mx::f2d_fast(Dy.lo), acc));
                     if (ND >= 2) acc = __fma_rn(dtq[DM], mx::f2d_fast(Dm.hi), __fma_rn(dtq[DM], mx::f2d_fast(Dm.lo), acc));
@@ -684,7 +718,7 @@ struct MinBlocks {
 template <class R, int ND, int STAGE, int TX, int TY, class S = double>
 __global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) stage_kernel(StageArgs a) {
     using T = Tile<ND, TX, TY>;
-    constexpr int NV = T::NV, PC = T::PC, NT = T::NT;
+    constexpr int NT = T::NT;
     constexpr int DM = ND - 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sW = reinterpret_cast<R *>(smem_raw);   // [NSLOT][NV][PC] primitives
@@ -754,7 +788,7 @@ struct MultiArgs {
 template <class R, int ND, int STAGE, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) multi_stage_kernel(MultiArgs a) {
     using T = Tile<ND, TX, TY>;
-    constexpr int NV = T::NV, PC = T::PC, NT = T::NT;
+    constexpr int NT = T::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sW = reinterpret_cast<R *>(smem_raw);
     R *sFx = sW + T::OFF_FX;
