@@ -497,6 +497,42 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 packed_done = true;
             }
         }
+        if constexpr (SINGLE) {  // all-FP32: dt L(U) of two fields per packed operation
+            const float *fxb = reinterpret_cast<const float *>(sFx) + ty * (TX + 1) + tx;
+            const float *fyb = reinterpret_cast<const float *>(sFy) + ty * TX + tx;
+#pragma unroll
+            for (int p = 0; p < (NV + 1) / 2; ++p) {
+                const int q0 = 2 * p, q1 = (2 * p + 1 < NV) ? 2 * p + 1 : 2 * p;
+                const float2 xl = make_float2(fxb[(size_t)q0 * T::NXF], fxb[(size_t)q1 * T::NXF]);
+                const float2 xh = make_float2(fxb[(size_t)q0 * T::NXF + 1], fxb[(size_t)q1 * T::NXF + 1]);
+                float2 acc = pk::mul2(pk::splat(c32x), pk::sub2(xl, xh));
+                if (ND == 3) {
+                    const float2 yl = make_float2(fyb[(size_t)q0 * T::NYF], fyb[(size_t)q1 * T::NYF]);
+                    const float2 yh = make_float2(fyb[(size_t)q0 * T::NYF + TX], fyb[(size_t)q1 * T::NYF + TX]);
+                    acc = pk::fma2(pk::splat(c32y), pk::sub2(yl, yh), acc);
+                }
+                if (ND >= 2) {
+                    const float2 ml = make_float2((float)Fmlo[q0], (float)Fmlo[q1]);
+                    const float2 mh = make_float2((float)Fmhi[q0], (float)Fmhi[q1]);
+                    acc = pk::fma2(pk::splat(c32m), pk::sub2(ml, mh), acc);
+                }
+#pragma unroll
+                for (int l = 0; l < 2; ++l) {
+                    const int q = 2 * p + l;
+                    if (q >= NV) break;
+                    const float a = l ? acc.y : acc.x;
+                    const float u = uc[q];
+                    float r;
+                    if (!HEUN2) r = __fadd_rn(u, a);
+                    else if (FROM_V) r = __fadd_rn(u, __fmul_rn(0.5f, a));  // u = V
+                    else r = __fmaf_rn(0.5f, u, __fmul_rn(0.5f, a));        // u = Un + U1
+                    un[q] = r;
+                    if constexpr (STORE_V) Uout[(long long)q * N + idx] = __fmul_rn(0.5f, __fadd_rn(u, r));
+                    else if (WRITE_U) Uout[(long long)q * N + idx] = r;
+                }
+            }
+            packed_done = true;
+        }
 #pragma unroll
         for (int q = 0; q < NV && !packed_done; ++q) {
             const R *fx = sFx + (size_t)q * T::NXF + ty * (TX + 1) + tx;
