@@ -95,17 +95,19 @@ __device__ __forceinline__ void clock_step(Clock *c, const Geom &g) {
 // for the normal component: 0 none, 1 negate (reflect), 2 min(v,0) (outflow,
 // low side), 3 max(v,0) (outflow, high side).  Ghosts within two cells follow
 // the boundary rules exactly; farther cells (only used by faces outside the
-// interior) are clamped into range.
+// interior) are clamped into range.  Callers pass -n <= x < 2n (a halo of two
+// cells around a tile of an axis with n >= 2 cells), so the periodic wrap is
+// one add or subtract.
 __device__ __forceinline__ int bc_map(int x, int n, int lo, int hi, int *act) {
     *act = 0;
     if (x >= 0 && x < n) return x;
     if (x < 0) {
-        if (lo == BC_PERIODIC) { int r = x % n; return r < 0 ? r + n : r; }
+        if (lo == BC_PERIODIC) return x + n;
         if (lo == BC_REFLECT) { *act = 1; int s = -x - 1; return s < n ? s : n - 1; }
         if (lo == BC_OUTFLOW) *act = 2;
         return 0;
     }
-    if (hi == BC_PERIODIC) return x % n;
+    if (hi == BC_PERIODIC) return x - n;
     if (hi == BC_REFLECT) { *act = 1; int s = 2 * n - 1 - x; return s >= 0 ? s : 0; }
     if (hi == BC_OUTFLOW) *act = 3;
     return n - 1;
