@@ -23,7 +23,7 @@ struct StageLaunch {
         int dev = 0, sms = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, smem)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cta_threads<R, ND, TX, TY>(), smem)) != cudaSuccess) return e;
         resident() = sms * (per_sm > 0 ? per_sm : 1);
         return cudaSuccess;
     }
@@ -38,7 +38,7 @@ struct StageLaunch {
         const long long nm = (ND >= 2) ? a.g.n[ND - 1] : 1;
         const long long total = ntx * nty * nm;
         const int grid = (int)(total < resident() ? total : resident());
-        stage_kernel<R, ND, STAGE, TX, TY, S><<<grid, TX * TY, smem, s>>>(a);
+        stage_kernel<R, ND, STAGE, TX, TY, S><<<grid, cta_threads<R, ND, TX, TY>(), smem, s>>>(a);
         return cudaGetLastError();
     }
 };
@@ -117,7 +117,7 @@ struct MultiLaunch {
         int dev = 0, sms = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, smem)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cta_threads<R, ND, TX, TY>(), smem)) != cudaSuccess) return e;
         resident() = sms * (per_sm > 0 ? per_sm : 1);
         return cudaSuccess;
     }
@@ -128,7 +128,7 @@ struct MultiLaunch {
         }
         constexpr size_t smem = Tile<ND, TX, TY>::template smem_bytes<R>();
         if (nblocks <= 0) return cudaSuccess;
-        multi_stage_kernel<R, ND, STAGE, TX, TY><<<nblocks, TX * TY, smem, s>>>(a);
+        multi_stage_kernel<R, ND, STAGE, TX, TY><<<nblocks, cta_threads<R, ND, TX, TY>(), smem, s>>>(a);
         return cudaGetLastError();
     }
 };

@@ -95,6 +95,19 @@ struct Tile {
                   "float2 accesses need even row, plane, flux-row and column strides");
 };
 
+// Threads per CTA.  The FP32 face loop of a 2D tile has TX + 1 face pairs
+// per row (march and x faces, each range padded to whole warps); with one
+// extra warp beyond the TX cell threads they all run in one round.  Every
+// other tile uses one thread per cell.
+template <class R, int ND, int TX, int TY>
+__host__ __device__ constexpr int cta_threads() {
+    return (std::is_same<R, float>::value && ND == 2)
+               ? ((TX / 2 + 31) / 32 * 32 + ((TX + 2) / 2 + 31) / 32 * 32 > TX * TY
+                      ? (TX / 2 + 31) / 32 * 32 + ((TX + 2) / 2 + 31) / 32 * 32
+                      : TX * TY)
+               : TX * TY;
+}
+
 // Asynchronous 4-byte global -> shared copy (no registers, no wait) and the
 // wait for all of this thread's outstanding copies.
 __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
@@ -128,6 +141,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     constexpr bool WRITE_W = STAGE == 3 || STAGE >= 5;           // stores the new state's primitives
     using T = Tile<ND, TX, TY>;
     constexpr int NV = T::NV, PX = T::PX, PC = T::PC, NT = T::NT;
+    constexpr int NTH = cta_threads<R, ND, TX, TY>();  // threads (>= NT; cells use the first NT)
     constexpr int DM = ND - 1;  // march axis (ND >= 2)
     const Consts<R> kc = make_consts<R>(g);
     const Consts<float> kc_f = make_consts<float>(g);
@@ -160,7 +174,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
         R *dst = sW + (size_t)slot * NV * PC;
         int actm = 0;  // the march-axis index map is the same for the whole plane
         const int cm = (ND >= 2) ? bc_map(L, g.n[DM], g.bc[DM][0], g.bc[DM][1], &actm) : 0;
-        for (int e = tid; e < PC; e += NT) {
+        for (int e = tid; e < PC; e += NTH) {
             const int hx = e % PX, hy = e / PX;
             if (hx >= wact + 4 || (ND == 3 && hy >= hact + 4)) continue;  // outside the active halo box
             int act[3] = {0, 0, 0};
@@ -223,7 +237,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
             R *dst = sW + (size_t)slot * NV * PC;
             int actm = 0;
             const int cm = (ND >= 2) ? bc_map(L, g.n[DM], g.bc[DM][0], g.bc[DM][1], &actm) : 0;
-            for (int e = tid; e < PC; e += NT) {
+            for (int e = tid; e < PC; e += NTH) {
                 const int hx = e % PX, hy = e / PX;
                 if (hx >= wact + 4 || (ND == 3 && hy >= hact + 4)) continue;
                 int act = 0;
@@ -251,7 +265,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
             if (ND >= 2) bc_map(L, g.n[DM], g.bc[DM][0], g.bc[DM][1], &actm);
             if (!x_rules && !y_rules && actm == 0) return;  // no ghost cell with a velocity rule
             R *dst = sW + (size_t)slot * NV * PC;
-            for (int e = tid; e < PC; e += NT) {
+            for (int e = tid; e < PC; e += NTH) {
                 const int hx = e % PX, hy = e / PX;
                 if (hx >= wact + 4 || (ND == 3 && hy >= hact + 4)) continue;
                 int act[3] = {0, 0, 0};
@@ -330,7 +344,7 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
         float *fyo = reinterpret_cast<float *>(sFy);
         const float *plane = cp + (size_t)(cur & 3) * NV * PC;
         const int ntask = inplane ? Y_END : M_END;
-        for (int k = tid; k < ntask; k += NT) {
+        for (int k = tid; k < ntask; k += NTH) {
             // gather: direction-specific, rotations fixed at compile time;
             // then one flux call site (keeps the kernel's code small)
             float2 st[4][NV];
@@ -746,15 +760,16 @@ __device__ __forceinline__ void reduce_to_clock(Clock *clk, unsigned flags, unsi
 // Mixed path: cap registers at 64 per thread so that 1024 threads per SM stay
 // resident (two 512-thread CTAs); the all-FP64 path is limited by shared
 // memory instead.
-template <class R, int NT>
+template <class R, int NT>  // NT: threads per CTA
 struct MinBlocks {
     static constexpr int value = std::is_same<R, float>::value ? (1024 / NT > 0 ? 1024 / NT : 1) : 1;
 };
 
 template <class R, int ND, int STAGE, int TX, int TY, class S = double>
-__global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) stage_kernel(StageArgs a) {
+__global__ void __launch_bounds__(cta_threads<R, ND, TX, TY>(), MinBlocks<R, cta_threads<R, ND, TX, TY>()>::value)
+    stage_kernel(StageArgs a) {
     using T = Tile<ND, TX, TY>;
-    constexpr int NT = T::NT;
+    constexpr int NTH = cta_threads<R, ND, TX, TY>();
     constexpr int DM = ND - 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sW = reinterpret_cast<R *>(smem_raw);   // [NSLOT][NV][PC] primitives
@@ -787,7 +802,7 @@ __global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) stage_ke
                                              reinterpret_cast<R *>(a.Wout), dtdx, a.cubic, x0, y0, k0, k1, sW, sFx,
                                              sFy, flags, floors, wmin);
     }
-    reduce_to_clock<STAGE, NT>(a.clk, flags, floors, wmin);
+    reduce_to_clock<STAGE, NTH>(a.clk, flags, floors, wmin);
 }
 
 // ---------------------------------------------------------------- many grids
@@ -822,9 +837,10 @@ struct MultiArgs {
 };
 
 template <class R, int ND, int STAGE, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) multi_stage_kernel(MultiArgs a) {
+__global__ void __launch_bounds__(cta_threads<R, ND, TX, TY>(), MinBlocks<R, cta_threads<R, ND, TX, TY>()>::value)
+    multi_stage_kernel(MultiArgs a) {
     using T = Tile<ND, TX, TY>;
-    constexpr int NT = T::NT;
+    constexpr int NTH = cta_threads<R, ND, TX, TY>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sW = reinterpret_cast<R *>(smem_raw);
     R *sFx = sW + T::OFF_FX;
@@ -843,7 +859,7 @@ __global__ void __launch_bounds__(TX *TY, MinBlocks<R, TX * TY>::value) multi_st
                                           reinterpret_cast<const R *>(a.Win) + gd->off,
                                           reinterpret_cast<R *>(a.Wout) + gd->off, dtdx, gd->cubic,
                                           sd.x0, sd.y0, sd.k0, sd.k1, sW, sFx, sFy, flags, floors, wmin);
-        reduce_to_clock<STAGE, NT>(clk, flags, floors, wmin);
+        reduce_to_clock<STAGE, NTH>(clk, flags, floors, wmin);
     }
 }
 
