@@ -115,6 +115,11 @@ __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) 
                  "l"(gmem_src)
                  : "memory");
 }
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // One segment: tile (x0, y0) of one grid, planes [k0, k1) of its march axis.
@@ -232,11 +237,31 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     // cp.async (issued one plane ahead, while the previous plane's cells are
     // updated); the ghost-zone velocity rules are applied by the copying
     // thread after its copies have landed (fix_plane).
+    // tiles whose halo box lies inside the grid copy whole rows in 8-byte
+    // pairs (the row start x0 - 2 is even, and so is every row and field
+    // offset when nx is even); the others copy cell by cell through the
+    // ghost-zone index map
+    const bool rows8 = x_inside && y_inside && (g.n[0] % 2 == 0);
     auto load_plane_async = [&](int L, int slot) {
         if constexpr (MIX && FROM_W) {
             R *dst = sW + (size_t)slot * NV * PC;
             int actm = 0;
             const int cm = (ND >= 2) ? bc_map(L, g.n[DM], g.bc[DM][0], g.bc[DM][1], &actm) : 0;
+            if (rows8) {
+                constexpr int CH = PX / 2;                        // 8-byte pairs per halo row
+                constexpr int NTASK = ((ND == 3) ? T::PY : 1) * CH;
+                // first halo cell (x0 - 2, y0 - 2) of plane cm; ND == 2: row cm
+                const long long row0 = ((ND == 3) ? ((long long)cm * g.n[1] + y0 - 2) * g.n[0]
+                                                  : (ND == 2 ? (long long)cm * g.n[0] : 0LL)) + x0 - 2;
+                for (int t = tid; t < NTASK; t += NTH) {
+                    const int hy = t / CH, ch = t % CH;
+                    const long long gi = row0 + (long long)hy * g.n[0] + 2 * ch;
+                    R *d = dst + hy * PX + 2 * ch;
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) cp_async8(d + (size_t)q * PC, Win + (long long)q * N + gi);
+                }
+                return;
+            }
             for (int e = tid; e < PC; e += NTH) {
                 const int hx = e % PX, hy = e / PX;
                 if (hx >= wact + 4 || (ND == 3 && hy >= hact + 4)) continue;
