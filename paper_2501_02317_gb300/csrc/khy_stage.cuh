@@ -362,6 +362,20 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     constexpr int X_END = M_END + (XPR * TY_ + 31) / 32 * 32;
     constexpr int Y_END = X_END + (YPC * (TX / 2) + 31) / 32 * 32;
     static_assert(TX % 2 == 0, "face pairs need an even tile width");
+    static_assert(NT % 4 == 0, "16-byte flux stores need a cell count divisible by 4");
+    // FP32 flux layout (mixed and FP32 paths), per direction: the fields in
+    // pairs (0,1), (2,3) as float2 arrays of nelem elements, an odd last
+    // field as a float array -- a cell reads two fields per 8-byte load
+    constexpr int NPR = NV / 2;
+    auto pread = [&](const float *base, int nelem, int p, int i) -> float2 {
+        if (p < NPR) return *reinterpret_cast<const float2 *>(base + (size_t)2 * nelem * p + 2 * i);
+        const float v = base[(size_t)2 * NPR * nelem + i];
+        return make_float2(v, v);
+    };
+    auto fread = [&](const float *base, int nelem, int q, int i) -> float {
+        if (q < 2 * NPR) return base[(size_t)2 * nelem * (q / 2) + 2 * i + (q & 1)];
+        return base[(size_t)2 * NPR * nelem + i];
+    };
     auto faces_mix = [&](int cur, bool inplane) {
         const float *cp = reinterpret_cast<const float *>(sW);
         float *fm = reinterpret_cast<float *>(sFm) + (size_t)(cur & 1) * NV * NT;
@@ -426,23 +440,40 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                     for (int j = 0; j < NV; ++j)
                         st[o][j] = *reinterpret_cast<const float2 *>(pl + (size_t)pk::rot_slot<ND>(1, j) * PC + o * PX);
             }
-            float2 Fr[NV];
+            float2 Fr[NV], Fq[NV];  // rotated order / field order
             pk::face_flux2<ND, PLM>(st, kc_f, Fr);
-            if (kind == 0) {
+            if (kind == 0) {  // columns a0, a0 + 1: one 16-byte store per field pair
 #pragma unroll
-                for (int j = 0; j < NV; ++j)
-                    *reinterpret_cast<float2 *>(fm + (size_t)pk::rot_slot<ND>(DM, j) * NT + a0) = Fr[j];
-            } else if (kind == 1) {
-                float *dst = fxo + a0 * (TX + 1) + a1;
+                for (int j = 0; j < NV; ++j) Fq[pk::rot_slot<ND>(DM, j)] = Fr[j];
 #pragma unroll
-                for (int j = 0; j < NV; ++j) {
-                    dst[(size_t)j * T::NXF] = Fr[j].x;
-                    if (vy) dst[(size_t)j * T::NXF + 1] = Fr[j].y;
+                for (int p = 0; p < NPR; ++p)
+                    *reinterpret_cast<float4 *>(fm + (size_t)2 * NT * p + 2 * a0) =
+                        make_float4(Fq[2 * p].x, Fq[2 * p + 1].x, Fq[2 * p].y, Fq[2 * p + 1].y);
+                if (NV % 2) *reinterpret_cast<float2 *>(fm + (size_t)2 * NPR * NT + a0) = Fq[NV - 1];
+            } else if (kind == 1) {  // faces a1, a1 + 1 of row a0
+#pragma unroll
+                for (int j = 0; j < NV; ++j) Fq[j] = Fr[j];  // rotation onto x is the identity
+                const int i = a0 * (TX + 1) + a1;
+#pragma unroll
+                for (int p = 0; p < NPR; ++p) {
+                    float *d = fxo + (size_t)2 * T::NXF * p + 2 * i;
+                    *reinterpret_cast<float2 *>(d) = make_float2(Fq[2 * p].x, Fq[2 * p + 1].x);
+                    if (vy) *reinterpret_cast<float2 *>(d + 2) = make_float2(Fq[2 * p].y, Fq[2 * p + 1].y);
                 }
-            } else {
-                float *dst = fyo + a1 * TX + a0;
+                if (NV % 2) {
+                    float *d = fxo + (size_t)2 * NPR * T::NXF + i;
+                    d[0] = Fq[NV - 1].x;
+                    if (vy) d[1] = Fq[NV - 1].y;
+                }
+            } else {  // face a1 of columns a0, a0 + 1
 #pragma unroll
-                for (int j = 0; j < NV; ++j) *reinterpret_cast<float2 *>(dst + (size_t)pk::rot_slot<ND>(1, j) * T::NYF) = Fr[j];
+                for (int j = 0; j < NV; ++j) Fq[pk::rot_slot<ND>(1, j)] = Fr[j];
+                const int i = a1 * TX + a0;
+#pragma unroll
+                for (int p = 0; p < NPR; ++p)
+                    *reinterpret_cast<float4 *>(fyo + (size_t)2 * T::NYF * p + 2 * i) =
+                        make_float4(Fq[2 * p].x, Fq[2 * p + 1].x, Fq[2 * p].y, Fq[2 * p + 1].y);
+                if (NV % 2) *reinterpret_cast<float2 *>(fyo + (size_t)2 * NPR * T::NYF + i) = Fq[NV - 1];
             }
         }
     };
@@ -490,6 +521,13 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
         const int gz = (ND == 3) ? cur : 0;
         if (gx >= g.n[0] || (ND == 3 && gy >= g.n[1])) return;
         const long long idx = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
+        // FP32 flux buffers (pair layout) around this cell
+        const float *fxs = reinterpret_cast<const float *>(sFx);
+        const float *fys = reinterpret_cast<const float *>(sFy);
+        const float *fml = reinterpret_cast<const float *>(sW + T::OFF_FM) + (size_t)((cur - 1) & 1) * NV * NT;
+        const float *fmh = reinterpret_cast<const float *>(sW + T::OFF_FM) + (size_t)(cur & 1) * NV * NT;
+        const int ix = ty * (TX + 1) + tx, iy = ty * TX + tx;
+        (void)fml; (void)fmh; (void)iy;
         // mixed, equal dx: the six face fluxes of each field summed exactly as
         // a float-float pair, two fields per packed operation (lanes), then
         // the FP64 update of those two fields
@@ -497,22 +535,16 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
         bool packed_done = false;
         if constexpr (MIX && !SINGLE) {
             if (cubic) {
-                const float *fxb = reinterpret_cast<const float *>(sFx) + ty * (TX + 1) + tx;
-                const float *fyb = reinterpret_cast<const float *>(sFy) + ty * TX + tx;
 #pragma unroll
                 for (int p = 0; p < (NV + 1) / 2; ++p) {
-                    const int q0 = 2 * p, q1 = (2 * p + 1 < NV) ? 2 * p + 1 : 2 * p;
-                    const float2 xl = make_float2(fxb[(size_t)q0 * T::NXF], fxb[(size_t)q1 * T::NXF]);
-                    const float2 xh = make_float2(fxb[(size_t)q0 * T::NXF + 1], fxb[(size_t)q1 * T::NXF + 1]);
+                    const float2 xl = pread(fxs, T::NXF, p, ix), xh = pread(fxs, T::NXF, p, ix + 1);
                     pk::FF2 Fs = pk::two_diff2(xl, xh);
                     if (ND == 3) {
-                        const float2 yl = make_float2(fyb[(size_t)q0 * T::NYF], fyb[(size_t)q1 * T::NYF]);
-                        const float2 yh = make_float2(fyb[(size_t)q0 * T::NYF + TX], fyb[(size_t)q1 * T::NYF + TX]);
+                        const float2 yl = pread(fys, T::NYF, p, iy), yh = pread(fys, T::NYF, p, iy + TX);
                         Fs = pk::ff_add2(Fs, pk::two_diff2(yl, yh));
                     }
                     if (ND >= 2) {
-                        const float2 ml = make_float2((float)Fmlo[q0], (float)Fmlo[q1]);
-                        const float2 mh = make_float2((float)Fmhi[q0], (float)Fmhi[q1]);
+                        const float2 ml = pread(fml, NT, p, tid), mh = pread(fmh, NT, p, tid);
                         Fs = pk::ff_add2(Fs, pk::two_diff2(ml, mh));
                     }
 #pragma unroll
@@ -537,22 +569,16 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
             }
         }
         if constexpr (SINGLE) {  // all-FP32: dt L(U) of two fields per packed operation
-            const float *fxb = reinterpret_cast<const float *>(sFx) + ty * (TX + 1) + tx;
-            const float *fyb = reinterpret_cast<const float *>(sFy) + ty * TX + tx;
 #pragma unroll
             for (int p = 0; p < (NV + 1) / 2; ++p) {
-                const int q0 = 2 * p, q1 = (2 * p + 1 < NV) ? 2 * p + 1 : 2 * p;
-                const float2 xl = make_float2(fxb[(size_t)q0 * T::NXF], fxb[(size_t)q1 * T::NXF]);
-                const float2 xh = make_float2(fxb[(size_t)q0 * T::NXF + 1], fxb[(size_t)q1 * T::NXF + 1]);
+                const float2 xl = pread(fxs, T::NXF, p, ix), xh = pread(fxs, T::NXF, p, ix + 1);
                 float2 acc = pk::mul2(pk::splat(c32x), pk::sub2(xl, xh));
                 if (ND == 3) {
-                    const float2 yl = make_float2(fyb[(size_t)q0 * T::NYF], fyb[(size_t)q1 * T::NYF]);
-                    const float2 yh = make_float2(fyb[(size_t)q0 * T::NYF + TX], fyb[(size_t)q1 * T::NYF + TX]);
+                    const float2 yl = pread(fys, T::NYF, p, iy), yh = pread(fys, T::NYF, p, iy + TX);
                     acc = pk::fma2(pk::splat(c32y), pk::sub2(yl, yh), acc);
                 }
                 if (ND >= 2) {
-                    const float2 ml = make_float2((float)Fmlo[q0], (float)Fmlo[q1]);
-                    const float2 mh = make_float2((float)Fmhi[q0], (float)Fmhi[q1]);
+                    const float2 ml = pread(fml, NT, p, tid), mh = pread(fmh, NT, p, tid);
                     acc = pk::fma2(pk::splat(c32m), pk::sub2(ml, mh), acc);
                 }
 #pragma unroll
@@ -577,10 +603,10 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
             const R *fx = sFx + (size_t)q * T::NXF + ty * (TX + 1) + tx;
             const R *fy = sFy + (size_t)q * T::NYF + ty * TX + tx;
             S r;
-            if constexpr (SINGLE) {  // all-FP32: U + dt L(U) in FP32, directions in x, y, z order
-                float acc = __fmul_rn(c32x, __fsub_rn(fx[0], fx[1]));
-                if (ND == 3) acc = __fmaf_rn(c32y, __fsub_rn(fy[0], fy[TX]), acc);
-                if (ND >= 2) acc = __fmaf_rn(c32m, __fsub_rn((float)Fmlo[q], (float)Fmhi[q]), acc);
+            if constexpr (SINGLE) {  // (the packed path above handles every FP32 update)
+                float acc = __fmul_rn(c32x, __fsub_rn(fread(fxs, T::NXF, q, ix), fread(fxs, T::NXF, q, ix + 1)));
+                if (ND == 3) acc = __fmaf_rn(c32y, __fsub_rn(fread(fys, T::NYF, q, iy), fread(fys, T::NYF, q, iy + TX)), acc);
+                if (ND >= 2) acc = __fmaf_rn(c32m, __fsub_rn(fread(fml, NT, q, tid), fread(fmh, NT, q, tid)), acc);
                 if (!HEUN2) r = __fadd_rn(uc[q], acc);
                 else if (FROM_V) r = __fadd_rn(uc[q], __fmul_rn(0.5f, acc));  // uc = V
                 else r = __fmaf_rn(0.5f, uc[q], __fmul_rn(0.5f, acc));   // uc = Un + U1
@@ -596,10 +622,10 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 const double u = uc[q];
                 {  // unequal dx (equal dx is the packed path above)
                     // F_lo - F_hi per direction, exact as float-float pairs
-                    const mx::FF Dx = mx::two_sum(fx[0], -fx[1]);
+                    const mx::FF Dx = mx::two_sum(fread(fxs, T::NXF, q, ix), -fread(fxs, T::NXF, q, ix + 1));
                     mx::FF Dy = {0.f, 0.f}, Dm = {0.f, 0.f};
-                    if (ND == 3) Dy = mx::two_sum(fy[0], -fy[TX]);
-                    if (ND >= 2) Dm = mx::two_sum(Fmlo[q], -Fmhi[q]);
+                    if (ND == 3) Dy = mx::two_sum(fread(fys, T::NYF, q, iy), -fread(fys, T::NYF, q, iy + TX));
+                    if (ND >= 2) Dm = mx::two_sum(fread(fml, NT, q, tid), -fread(fmh, NT, q, tid));
                     double acc = __fma_rn(dtq[0], mx::f2d_fast(Dx.hi), __dmul_rn(dtq[0], mx::f2d_fast(Dx.lo)));
                     if (ND == 3) acc = __fma_rn(dtq[1], mx::f2d_fast(Dy.hi), __fma_rn(dtq[1], mx::f2d_fast(Dy.lo), acc));
                     if (ND >= 2) acc = __fma_rn(dtq[DM], mx::f2d_fast(Dm.hi), __fma_rn(dtq[DM], mx::f2d_fast(Dm.lo), acc));
@@ -673,13 +699,8 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
             __syncthreads();
             if (L + 1 <= k1 + 1) load_plane_async(L + 1, (L + 1) & 3);  // slot of plane cur - 1, now free
             if (cur >= k0 && own) {
-                R Fmlo[NV], Fmhi[NV];
-#pragma unroll
-                for (int q = 0; q < NV; ++q) {
-                    Fmlo[q] = sFm[(size_t)((cur - 1) & 1) * NV * NT + (size_t)q * NT + tid];
-                    Fmhi[q] = sFm[(size_t)(cur & 1) * NV * NT + (size_t)q * NT + tid];
-                }
-                update_cell(cur, Fmlo, Fmhi, uc, ub);
+                R unused[NV];  // the FP32 update reads the march fluxes from sFm itself
+                update_cell(cur, unused, unused, uc, ub);
             }
         }
     } else if constexpr (MIX) {
@@ -691,15 +712,10 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 faces_mix(cur, cur >= k0);
                 __syncthreads();
                 if (cur >= k0 && tx < wact && ty < hact) {
-                    R Fmlo[NV], Fmhi[NV];
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) {
-                        Fmlo[q] = sFm[(size_t)((cur - 1) & 1) * NV * NT + (size_t)q * NT + tid];
-                        Fmhi[q] = sFm[(size_t)(cur & 1) * NV * NT + (size_t)q * NT + tid];
-                    }
+                    R unused[NV];  // the FP32 update reads the march fluxes from sFm itself
                     S uc[NV], ub[NV];
                     prefetch_cell(cur, uc, ub);
-                    update_cell(cur, Fmlo, Fmhi, uc, ub);
+                    update_cell(cur, unused, unused, uc, ub);
                 }
             } else {
                 __syncthreads();
