@@ -69,6 +69,27 @@ __device__ __forceinline__ double f2d_fast(float x) {
     return __hiloint2double((int)hi, (int)(f << 29));
 }
 
+// hi + lo of a float-float pair (|lo| <= ulp(hi)/2, as TwoSum and its
+// renormalisation produce) as one double, with integer operations only:
+// lo's significand is shifted into the 29 low significand bits that the
+// double of hi leaves zero and added (same sign) or subtracted (opposite
+// sign; from an exact power of two the result drops a binade, where the
+// unit halves).  Exact when the exponents differ by at most 29, otherwise
+// truncated below 2^-52 relative; a subnormal lo is dropped.  Replaces an
+// FP64 add in the update.
+__device__ __forceinline__ double ff_to_double(float hi, float lo) {
+    const unsigned H = __float_as_uint(hi), L = __float_as_uint(lo);
+    const unsigned el = (L >> 23) & 0xFFu;
+    const int d = (int)((H >> 23) & 0xFFu) - (int)el;  // >= 24 for a normalised pair
+    const unsigned ml = (L & 0x7FFFFFu) | 0x800000u;
+    unsigned lp = d <= 29 ? ml << min(29 - d, 31) : ml >> min(d - 29, 31);
+    if (el == 0u || (H & 0x7FFFFFFFu) == 0u) lp = 0u;  // lo zero (or subnormal), or hi zero
+    const bool same = ((H ^ L) & 0x80000000u) == 0u;
+    if (!same && (H & 0x7FFFFFu) == 0u) lp <<= 1;
+    const long long b = __double_as_longlong(f2d_fast(hi));
+    return __longlong_as_double(same ? b + (long long)lp : b - (long long)lp);
+}
+
 // |x| -> float rounded toward zero, for estimates only (the CFL candidate of
 // the van Leer corrector): magnitudes below 2^-126 flush to zero; |x| must
 // stay below 2^128.

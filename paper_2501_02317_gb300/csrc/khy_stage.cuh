@@ -555,8 +555,9 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                         const double u = uc[q];
                         double r;
                         if (!HEUN2) {
-                            const double lo = mx::f2d_fast(__fmul_rn(c32, flo));
-                            r = __fma_rn(dtq[0], mx::f2d_fast(fhi), __dadd_rn(u, lo));
+                            // one FP64 operation: the flux sum as one double
+                            // built with integer operations
+                            r = __fma_rn(dtq[0], mx::ff_to_double(fhi, flo), u);
                         } else {  // u = Un + U1
                             const double lo = mx::f2d_fast(__fmul_rn(hc32, flo));
                             r = __fma_rn(hcd, mx::f2d_fast(fhi), __fma_rn(0.5, u, lo));
