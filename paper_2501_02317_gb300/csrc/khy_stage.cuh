@@ -31,22 +31,25 @@
 // launch is persistent: one CTA per resident slot, and CTA b owns the b-th
 // equal share of the (tile, plane) sequence, so every SM gets the same number
 // of planes.  A CTA walks each of its tile segments plane by plane: a plane
-// of the conserved state with a two-cell halo on every side is loaded once,
-// converted to primitives (Sec. 3.1) with the ghost-zone rules applied by
-// index mapping (Sec. 3.1.1), and kept in a four-plane ring in shared memory
-// (the row staging of Sec. 3.2.1 extended to a 2.5D march).  In-plane face
-// fluxes run as one flat task list over the CTA; the face along the march
-// axis is computed by the thread that owns the column.  Each face flux is
-// computed once per CTA and enters its two cells with opposite signs; faces
-// on a tile edge are recomputed by the neighbouring CTA from the same inputs
-// by the same code, so both cells see the same value.
+// of primitives with a two-cell halo on every side -- copied from the stored
+// primitives (cp.async, one plane ahead) or recovered from the state (Sec.
+// 3.1) -- with the ghost-zone rules applied by index mapping (Sec. 3.1.1) is
+// kept in a four-plane ring in shared memory (the row staging of Sec. 3.2.1
+// extended to a 2.5D march).  FP32 fluxes: the march, x and y faces of a
+// plane are warp-aligned task ranges, two faces per task (packed FP32x2);
+// FP64 fluxes: in-plane faces as one task list, the march face by the
+// column's thread.  Each face flux is computed once per CTA and enters its
+// two cells with opposite signs; faces on a tile edge are recomputed by the
+// neighbouring CTA from the same inputs by the same code, so both cells see
+// the same value.
 //
-// Precision (Sec. 3.2.2) is the template parameter R:
+// Precision (Sec. 3.2.2) is the template parameter R (fluxes) with S (state):
 //   R = double : all-FP64, every operation in the CPU reference's order
 //                (compiled with -fmad=false: bitwise equal to the reference);
-//   R = float  : mixed -- FP32 reconstruction and HLLC, FP64 state, FP64
-//                internal energy in the recovery and FP64 flux-difference
-//                accumulation (khy_mixed_kernels.cuh).
+//   R = float  : mixed (S = double) -- FP32 reconstruction and HLLC, FP64
+//                state, FP64 internal energy in the recovery and FP64
+//                flux-difference accumulation (khy_mixed_kernels.cuh); or
+//                all-FP32 (S = float).
 #pragma once
 
 #include <type_traits>
