@@ -90,6 +90,22 @@ __device__ __forceinline__ double ff_to_double(float hi, float lo) {
     return __longlong_as_double(same ? b + (long long)lp : b - (long long)lp);
 }
 
+// x / 2 by decrementing the exponent with integer operations: exact for
+// |x| >= 2^-1021 (where halving is exact in FP64 as well); zeros keep their
+// sign, smaller magnitudes flush to a signed zero; Inf and NaN pass through.
+// Replaces an FP64 multiply in the Heun average.
+__device__ __forceinline__ double half_exact(double x) {
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const unsigned e = (unsigned)hi & 0x7FF00000u;
+    int h = hi - 0x00100000, l = lo;
+    if (e <= 0x00100000u) {
+        h = hi & (int)0x80000000u;
+        l = 0;
+    }
+    if (e == 0x7FF00000u) h = hi;
+    return __hiloint2double(h, l);
+}
+
 // |x| -> float rounded toward zero, for estimates only (the CFL candidate of
 // the van Leer corrector): magnitudes below 2^-126 flush to zero; |x| must
 // stay below 2^128.

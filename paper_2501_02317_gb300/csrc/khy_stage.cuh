@@ -20,9 +20,11 @@
 // Single-grid Heun steps keep the primitives of the current state in HBM
 // (in the flux precision) so that no CTA recovers halo cells:
 //   stage_kernel 5 : as stage 1, fluxes from the stored primitives of Un;
-//                    writes U1 and the primitives of U1
+//                    writes the primitives of U1 and, in the U1 buffer, U1
+//                    (all-FP64) or V = (Un + U1)/2 (mixed and all-FP32)
 //   stage_kernel 6 : as stage 2, fluxes from the stored primitives of U1;
-//                    writes Un+1 and its primitives.
+//                    writes Un+1 (from V alone where V was stored) and its
+//                    primitives.
 // Every stored primitive comes from the same recovery function as an on-the-
 // fly one, so stages 5, 6 give the same bits as stages 1, 2.
 //
@@ -487,15 +489,15 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     // candidate (last stage of a step).
     // the cell's state values, loaded ahead of the barrier that precedes the
     // update: uc = the state this stage adds to; for the Heun average, ub = Un
-    // (all-FP64: kept apart for the reference operation order) or, mixed and
-    // FP32, uc = Un + U1 already summed (fewer live registers).
-    // The all-FP32 stage 5 stores V = (Un + U1) / 2 (exact halving) in place
-    // of U1 -- its primitives are stored as well -- so stage 6 adds to V and
-    // reads no Un: V + acc/2 equals fma(0.5, Un + U1, acc/2) bit for bit.  (In
-    // the mixed path the extra FP64 add in stage 5 costs more than the Un
-    // read it saves in stage 6.)
-    constexpr bool STORE_V = SINGLE && STAGE == 5;
-    constexpr bool FROM_V = SINGLE && STAGE == 6;
+    // (all-FP64: kept apart for the reference operation order), or in the
+    // mixed and FP32 stage 2 uc = Un + U1 already summed (fewer live
+    // registers), or in stage 6 uc = V.
+    // Stage 5 of the mixed and all-FP32 paths stores V = (Un + U1) / 2
+    // (exact halving) in place of U1 -- the primitives of U1 are stored as
+    // well -- so stage 6 adds to V and reads no Un: V + acc/2 equals the
+    // lean stage 2's half(Un + U1) + acc/2 bit for bit.
+    constexpr bool STORE_V = MIX && STAGE == 5;
+    constexpr bool FROM_V = MIX && STAGE == 6;
     constexpr bool SUM_A = MIX && HEUN2 && !FROM_V;
     auto prefetch_cell = [&](int cur, S (&uc)[NV], S (&ub)[NV]) {
         const int gx = x0 + tx;
@@ -557,16 +559,15 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                         const float fhi = l ? Fs.hi.y : Fs.hi.x, flo = l ? Fs.lo.y : Fs.lo.x;
                         const double u = uc[q];
                         double r;
-                        if (!HEUN2) {
-                            // one FP64 operation: the flux sum as one double
-                            // built with integer operations
-                            r = __fma_rn(dtq[0], mx::ff_to_double(fhi, flo), u);
-                        } else {  // u = Un + U1
-                            const double lo = mx::f2d_fast(__fmul_rn(hc32, flo));
-                            r = __fma_rn(hcd, mx::f2d_fast(fhi), __fma_rn(0.5, u, lo));
-                        }
+                        // one FP64 operation: the flux sum as one double
+                        // built with integer operations
+                        const double fs = mx::ff_to_double(fhi, flo);
+                        if (!HEUN2) r = __fma_rn(dtq[0], fs, u);
+                        else if (FROM_V) r = __fma_rn(hcd, fs, u);        // u = V
+                        else r = __fma_rn(hcd, fs, mx::half_exact(u));   // u = Un + U1
                         un[q] = r;
-                        if (WRITE_U) Uout[(long long)q * N + idx] = r;
+                        if constexpr (STORE_V) Uout[(long long)q * N + idx] = mx::half_exact(__dadd_rn(u, r));
+                        else if (WRITE_U) Uout[(long long)q * N + idx] = r;
                     }
                 }
                 packed_done = true;
@@ -634,12 +635,14 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                     if (ND == 3) acc = __fma_rn(dtq[1], mx::f2d_fast(Dy.hi), __fma_rn(dtq[1], mx::f2d_fast(Dy.lo), acc));
                     if (ND >= 2) acc = __fma_rn(dtq[DM], mx::f2d_fast(Dm.hi), __fma_rn(dtq[DM], mx::f2d_fast(Dm.lo), acc));
                     if (!HEUN2) r = __dadd_rn(u, acc);
-                    else r = __fma_rn(0.5, u, __dmul_rn(0.5, acc));  // u = Un + U1
+                    else if (FROM_V) r = __fma_rn(0.5, acc, u);                // u = V
+                    else r = __fma_rn(0.5, acc, mx::half_exact(u));            // u = Un + U1
                 }
             }
             un[q] = r;
             if constexpr (STORE_V) {
-                Uout[(long long)q * N + idx] = __fmul_rn(0.5f, __fadd_rn(uc[q], r));
+                if constexpr (SINGLE) Uout[(long long)q * N + idx] = __fmul_rn(0.5f, __fadd_rn(uc[q], r));
+                else Uout[(long long)q * N + idx] = mx::half_exact(__dadd_rn(uc[q], r));
             } else if (WRITE_U) {
                 Uout[(long long)q * N + idx] = r;
             }
