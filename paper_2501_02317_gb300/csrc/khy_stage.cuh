@@ -38,7 +38,7 @@
 // 3.1) -- with the ghost-zone rules applied by index mapping (Sec. 3.1.1) is
 // kept in a four-plane ring in shared memory (the row staging of Sec. 3.2.1
 // extended to a 2.5D march).  FP32 fluxes: the march, x and y faces of a
-// plane are warp-aligned task ranges, two faces per task (packed FP32x2);
+// plane are consecutive task ranges, two faces per task (packed FP32x2);
 // FP64 fluxes: in-plane faces as one task list, the march face by the
 // column's thread.  Each face flux is computed once per CTA and enters its
 // two cells with opposite signs; faces on a tile edge are recomputed by the
@@ -101,9 +101,9 @@ struct Tile {
 };
 
 // Threads per CTA.  The FP32 face loop of a 2D tile has TX + 1 face pairs
-// per row (march and x faces, each range padded to whole warps); with one
-// extra warp beyond the TX cell threads they all run in one round.  Every
-// other tile uses one thread per cell.
+// per row (TX/2 march-face pairs, TX/2 + 1 x-face pairs); with the TX cell
+// threads rounded up to whole warps for each range they all run in one
+// round.  Every other tile uses one thread per cell.
 template <class R, int ND, int TX, int TY>
 __host__ __device__ constexpr int cta_threads() {
     return (std::is_same<R, float>::value && ND == 2)
@@ -347,9 +347,11 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     };
 
     // mixed path: the faces of one plane as three direction-specific task
-    // ranges -- march-axis faces, x faces, y faces -- each padded to whole
-    // warps, so a warp always works on one direction and every rotation is a
-    // compile-time constant.  A task computes two neighbouring faces of one
+    // ranges -- march-axis faces, x faces, y faces -- back to back: each
+    // branch's rotation is a compile-time constant, a warp that straddles two
+    // ranges diverges only in its gather and its stores and runs the one
+    // flux call site for both (no warp runs the flux for a few lanes of
+    // padding).  A task computes two neighbouring faces of one
     // direction as the two lanes of the packed face_flux2, from one shared
     // stencil: x faces f, f+1 of one row share a five-cell stencil (three
     // float2 loads); y faces and march faces of the column pair (2c, 2c+1)
@@ -363,9 +365,9 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     constexpr int YPC = (ND == 3) ? TY + 1 : 0;        // y faces per column pair (faces 0..TY)
     constexpr int TY_ = (ND == 3) ? TY : 1;
     constexpr int NMP = (ND >= 2) ? NT / 2 : 0;        // march-face column pairs
-    constexpr int M_END = (NMP + 31) / 32 * 32;
-    constexpr int X_END = M_END + (XPR * TY_ + 31) / 32 * 32;
-    constexpr int Y_END = X_END + (YPC * (TX / 2) + 31) / 32 * 32;
+    constexpr int M_END = NMP;
+    constexpr int X_END = M_END + XPR * TY_;
+    constexpr int Y_END = X_END + YPC * (TX / 2);
     static_assert(TX % 2 == 0, "face pairs need an even tile width");
     static_assert(NT % 4 == 0, "16-byte flux stores need a cell count divisible by 4");
     // FP32 flux layout (mixed and FP32 paths), per direction: the fields in
