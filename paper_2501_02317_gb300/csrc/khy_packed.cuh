@@ -89,7 +89,8 @@ __device__ __forceinline__ void hllc2(const Consts<float> &k, const float2 (&wl)
     cl = make_float2(xl.x > 0.f ? cl.x : 0.f, xl.y > 0.f ? cl.y : 0.f);
     cr = make_float2(xr.x > 0.f ? cr.x : 0.f, xr.y > 0.f ? cr.y : 0.f);
     const float2 du = sub2(ur, ul);
-    const float2 ppv = sub2(mul2(splat(0.5f), add2(pl, pr)), mul2(mul2(mul2(splat(0.125f), du), add2(rl, rr)), add2(cl, cr)));
+    // p_pvrs = (p_L + p_R)/2 - (u_R - u_L)(rho_L + rho_R)(c_L + c_R)/8
+    const float2 ppv = mul2(splat(0.5f), fma2(mul2(du, add2(rl, rr)), mul2(splat(-0.25f), add2(cl, cr)), add2(pl, pr)));
     float2 pstar = max2(ppv, splat(0.f));
     const float2 pmax = max2(pl, pr);
     const bool tx = pstar.x > pmax.x, ty = pstar.y > pmax.y;
@@ -105,12 +106,15 @@ __device__ __forceinline__ void hllc2(const Consts<float> &k, const float2 (&wl)
     const float2 ratr = max2(div2(pstar, pr), one);
     const float2 ql = root2_ge1(fma2(splat(k.g1), sub2(ratl, one), one));  // rat >= 1
     const float2 qr = root2_ge1(fma2(splat(k.g1), sub2(ratr, one), one));
-    const float2 dsl = mul2(splat(-1.f), mul2(cl, ql));
+    // Eq. 4: Delta s_K = s_K - u_K straight from c_K q_K
+    const float2 dsl = mul2(mul2(splat(-1.f), cl), ql);
     const float2 dsr = mul2(cr, qr);
     const float2 sl = add2(ul, dsl);
     const float2 sr = add2(ur, dsr);
-    const float2 sstar = div2(sub2(sub2(pr, mul2(mul2(rr, ur), dsr)), sub2(pl, mul2(mul2(rl, ul), dsl))),
-                              sub2(mul2(rl, dsl), mul2(rr, dsr)));
+    // m_K = rho_K Delta s_K, then Eq. 5:
+    // s* = (p_R - p_L + u_L m_L - u_R m_R) / (m_L - m_R)
+    const float2 ml = mul2(rl, dsl), mr = mul2(rr, dsr);
+    const float2 sstar = div2(sub2(fma2(ul, ml, sub2(pr, pl)), mul2(ur, mr)), sub2(ml, mr));
     // branch order: 0 <= s_L -> F_L; 0 <= s* -> F*_L; 0 < s_R -> F*_R; else F_R
     const bool lx = (0.f <= sl.x) || (0.f <= sstar.x), ly = (0.f <= sl.y) || (0.f <= sstar.y);
     const bool ox = lx ? (0.f <= sl.x) : !(0.f < sr.x), oy = ly ? (0.f <= sl.y) : !(0.f < sr.y);
@@ -119,33 +123,28 @@ __device__ __forceinline__ void hllc2(const Consts<float> &k, const float2 (&wl)
     for (int j = 0; j < NT + 3; ++j) w[j] = sel2(lx, ly, wl[j], wr[j]);
     const float2 rk = w[0], uk = w[1], pk = w[P];
     const float2 sk = sel2(lx, ly, sl, sr);
-    const float2 dsk = sel2(lx, ly, dsl, dsr);
+    const float2 mk = sel2(lx, ly, ml, mr);
     float2 vsq = mul2(uk, uk);
 #pragma unroll
     for (int j = 0; j < NT; ++j) vsq = fma2(w[2 + j], w[2 + j], vsq);
     const float2 E = fma2(mul2(splat(0.5f), rk), vsq, mul2(pk, splat(k.igm1)));
     const float2 mf = mul2(rk, uk);
-    float2 Uk[NT + 3], Fk[NT + 3];
-    Uk[0] = rk;
-    Uk[1] = mf;
-    Fk[0] = mf;
-    Fk[1] = fma2(mf, uk, pk);
+    // F_K, and F = F_K + s_K (U*_K - U_K) with s_K and the star factor
+    // rho_K Delta s_K / (s_K - s*) zeroed where F_K itself is the flux
+    // (supersonic lanes: the correction vanishes exactly and stays finite)
+    const float2 zero = splat(0.f);
+    const float2 skm = sel2(ox, oy, zero, sk);
+    const float2 fac = sel2(ox, oy, zero, div2(mk, sub2(sk, sstar)));
+    const float2 d0 = sub2(fac, rk);  // rho*_K - rho_K; transverse: (rho*_K - rho_K) t
+    const float2 sd0 = mul2(skm, d0);
+    F[0] = add2(mf, sd0);
+    F[1] = fma2(skm, sub2(mul2(fac, sstar), mf), fma2(mf, uk, pk));
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
-        Uk[2 + j] = mul2(rk, w[2 + j]);
-        Fk[2 + j] = mul2(mf, w[2 + j]);
-    }
-    Uk[P] = E;
-    Fk[P] = mul2(add2(E, pk), uk);
-    const float2 fac = div2(mul2(rk, dsk), sub2(sk, sstar));
-    float2 Us[NT + 3];
-    Us[0] = fac;
-    Us[1] = mul2(fac, sstar);
-#pragma unroll
-    for (int j = 0; j < NT; ++j) Us[2 + j] = mul2(fac, w[2 + j]);
-    Us[P] = mul2(fac, fma2(sub2(sstar, uk), add2(sstar, div2(pk, mul2(rk, dsk))), div2(Uk[P], rk)));
-#pragma unroll
-    for (int q = 0; q < NT + 3; ++q) F[q] = sel2(ox, oy, Fk[q], fma2(sk, sub2(Us[q], Uk[q]), Fk[q]));
+    for (int j = 0; j < NT; ++j) F[2 + j] = fma2(sd0, w[2 + j], mul2(mf, w[2 + j]));
+    // E*_K / rho*_K = E_K / rho_K + (s* - u_K)(s* + p_K / m_K)
+    const float2 X = fma2(sub2(sstar, uk), fma2(pk, make_float2(rcp_approx(mk.x), rcp_approx(mk.y)), sstar),
+                          mul2(E, make_float2(rcp_approx(rk.x), rcp_approx(rk.y))));
+    F[P] = fma2(skm, sub2(mul2(fac, X), E), mul2(add2(E, pk), uk));
 }
 
 // Storage slot of rotated component j (0 rho, 1 normal velocity, 2..ND
