@@ -80,10 +80,12 @@ __device__ __forceinline__ double f2d_fast(float x) {
 __device__ __forceinline__ double ff_to_double(float hi, float lo) {
     const unsigned H = __float_as_uint(hi), L = __float_as_uint(lo);
     const unsigned el = (L >> 23) & 0xFFu;
-    const int d = (int)((H >> 23) & 0xFFu) - (int)el;  // >= 24 for a normalised pair
-    const unsigned ml = (L & 0x7FFFFFu) | 0x800000u;
-    unsigned lp = d <= 29 ? ml << min(29 - d, 31) : ml >> min(d - 29, 31);
-    if (el == 0u || (H & 0x7FFFFFFFu) == 0u) lp = 0u;  // lo zero (or subnormal), or hi zero
+    // exponent gap d - 24 (>= 0 for a normalised pair; hi = 0 wraps to a
+    // large shift): lo's 24-bit significand moved up 5 bits, then down by
+    // d - 24, sits d - 29 bits below the 29-bit boundary -- one shift either way
+    const unsigned k = min(((H >> 23) & 0xFFu) - el - 24u, 31u);
+    unsigned lp = (((L & 0x7FFFFFu) | 0x800000u) << 5) >> k;
+    if (el == 0u) lp = 0u;  // lo zero (or subnormal)
     const bool same = ((H ^ L) & 0x80000000u) == 0u;
     if (!same && (H & 0x7FFFFFu) == 0u) lp <<= 1;
     const long long b = __double_as_longlong(f2d_fast(hi));
