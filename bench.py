@@ -127,11 +127,12 @@ class ClockSampler:
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
 
-def cpu_oracle_rate(seconds: float = 10.0, n: int = 128):
-    """Oracle cell-updates/s on an n^3 turbulence box with all host cores."""
+def cpu_oracle_rate(seconds: float = 10.0, n: int = 128, threads: int = 0):
+    """Oracle cell-updates/s on an n^3 turbulence box with `threads` host
+    threads (0: all cores); at least one step."""
     import oracle
     from paper_2501_02317_gb300 import workloads as wl
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     used = oracle.set_threads(cores)
     mesh, W = wl.turbulence(n, prec=wl.PREC_FP64)
     U = oracle.prim_to_cons(mesh, W)
@@ -385,6 +386,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         v, cores, sample = cpu_oracle_rate()
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        # the plain single-thread oracle beside the OpenMP build (same bits)
+        v1, _, sample1 = cpu_oracle_rate(seconds=5.0, threads=1)
+        cpu["single_thread"] = {"value": v1, "unit": UNIT, "cores": 1, "sample": sample1}
 
     if rank == 0:
         line = {
