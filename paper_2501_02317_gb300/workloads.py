@@ -148,6 +148,29 @@ def sound_wave(n: int, amp: float = 1e-6, p0: float = 5.0 / 3.0, rho0: float = 1
     return mesh, W
 
 
+def advection_wave(n: int, kind: str = "contact", profile: str = "sine", amp: float = 0.1,
+                   v: float = 1.0, rho0: float = 1.0, p0: float = 5.0 / 3.0, gamma: float = 5.0 / 3.0,
+                   cfl: float = 0.4, prec: int = PREC_FP64) -> Tuple[Mesh, np.ndarray]:
+    """Sec. 4.1 wave tests on a periodic unit box, background (rho0, p0) moving
+    with v along x: a contact wave (drho) or a shear wave (dv_y; a 2D grid n x 2),
+    the perturbation A sin(2 pi x) ("sine") or A where x < 0.5 ("tophat")."""
+    if kind not in ("contact", "shear") or profile not in ("sine", "tophat"):
+        raise ValueError("kind is contact or shear, profile is sine or tophat")
+    ndim = 1 if kind == "contact" else 2
+    mesh = Mesh(ndim=ndim, n=(n, 1 if ndim == 1 else 2, 1), gamma=gamma, cfl=cfl,
+                bc=_all_bc(BC_PERIODIC), prec=prec)
+    x = _grids(mesh)[0]
+    d = amp * np.sin(2.0 * np.pi * x) if profile == "sine" else np.where(x < 0.5, amp, 0.0)
+    d = np.broadcast_to(d, mesh.shape[1:])
+    W = _empty(mesh)
+    W[0] = rho0 + d if kind == "contact" else rho0
+    W[1] = v
+    if kind == "shear":
+        W[2] = d
+    W[mesh.nvar - 1] = p0
+    return mesh, W
+
+
 def sound_speed(p0: float, rho0: float, gamma: float) -> float:
     return math.sqrt(gamma * p0 / rho0)
 
