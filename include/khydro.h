@@ -232,7 +232,9 @@ khy_status khy_batch_get_clock(khy_batch *b, int grid, double *t, long *steps, d
  * shape (ndim, prec, grid count, cell count).  Synchronises. */
 khy_status khy_batch_autotune(khy_batch *b, int trial_steps, int *variant, float *ms_per_step);
 
-/* Selects a tile variant explicitly (0..2; see khy_batch_info). */
+/* Selects a tile variant explicitly: 1D 0..1 (rows of 128, 256), 2D 0..4
+ * (rows of 64, 128, 256, 124, 252), 3D 0..2 (32x8, 32x16, 64x8); see
+ * khy_batch_info.  Other values: KHY_ERR_ARG. */
 khy_status khy_batch_set_variant(khy_batch *b, int variant);
 
 /* Like khy_profile_steps for a batch: average ms of the clock, stage-1 and

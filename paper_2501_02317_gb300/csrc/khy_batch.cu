@@ -323,8 +323,11 @@ void build_segments(const std::vector<int> &ids, const std::vector<Geom> &geoms,
 }
 
 void multi_variant_tile(int ndim, int variant, int *tx, int *ty) {
-    static const int table[4][kMultiVariants][2] = {
-        {{0, 0}, {0, 0}, {0, 0}}, {{128, 1}, {256, 1}, {0, 0}}, {{64, 1}, {128, 1}, {256, 1}}, {{32, 8}, {32, 16}, {64, 8}}};
+    // the same shapes as variant_tile() of the kernels (tx = 0: none)
+    static const int table[4][kMultiVariants][2] = {{{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
+                                                    {{128, 1}, {256, 1}, {0, 0}, {0, 0}, {0, 0}},
+                                                    {{64, 1}, {128, 1}, {256, 1}, {124, 1}, {252, 1}},
+                                                    {{32, 8}, {32, 16}, {64, 8}, {0, 0}, {0, 0}}};
     *tx = *ty = 0;
     if (ndim < 1 || ndim > 3 || variant < 0 || variant >= kMultiVariants) return;
     *tx = table[ndim][variant][0];

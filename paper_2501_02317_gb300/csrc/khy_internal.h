@@ -30,7 +30,7 @@ cudaError_t prepare_single(int ndim);
 // variants of each dimensionality are listed by multi_variant_tile (the
 // autotuner times them and picks one).  nblocks is the CTA count of the
 // segment schedule (at most multi_resident).
-constexpr int kMultiVariants = 3;
+constexpr int kMultiVariants = 5;
 void multi_variant_tile(int ndim, int variant, int *tx, int *ty);  // tx = 0: no such variant
 int multi_resident(bool fp64, int ndim, int variant);              // resident CTAs, 0 on error
 cudaError_t launch_multi_stage(bool fp64, const MultiArgs &a, int ndim, int variant, int stage, int nblocks,

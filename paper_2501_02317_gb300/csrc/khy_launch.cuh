@@ -49,7 +49,7 @@ template <> struct TileOf<double, 1> { static constexpr int TX = 128, TY = 1; };
 template <> struct TileOf<double, 2> { static constexpr int TX = 128, TY = 1; };
 template <> struct TileOf<double, 3> { static constexpr int TX = 32, TY = 8; };
 template <> struct TileOf<float, 1> { static constexpr int TX = 256, TY = 1; };
-template <> struct TileOf<float, 2> { static constexpr int TX = 256, TY = 1; };
+template <> struct TileOf<float, 2> { static constexpr int TX = 124, TY = 1; };  // 125 face-pair tasks: 4 whole warps
 template <> struct TileOf<float, 3> { static constexpr int TX = 32, TY = 8; };
 
 template <class R, int ND, int STAGE, class S = double>
@@ -133,11 +133,15 @@ struct MultiLaunch {
     }
 };
 
-// variant table: tile shapes per dimensionality
+// variant table: tile shapes per dimensionality.  The 2D widths 124 and 252
+// give the FP32 face loop 125 and 253 face-pair tasks per row (TX/2 march,
+// TX/2 + 1 x) -- 4 and 8 whole warps -- where 128 and 256 give 129 and 257
+// and one more warp-round of flux code for a single task.
 struct VariantTile { int tx, ty; };
 __host__ __device__ constexpr VariantTile variant_tile(int ndim, int v) {
     return ndim == 1 ? (v == 0 ? VariantTile{128, 1} : v == 1 ? VariantTile{256, 1} : VariantTile{0, 0})
-         : ndim == 2 ? (v == 0 ? VariantTile{64, 1} : v == 1 ? VariantTile{128, 1} : v == 2 ? VariantTile{256, 1} : VariantTile{0, 0})
+         : ndim == 2 ? (v == 0 ? VariantTile{64, 1} : v == 1 ? VariantTile{128, 1} : v == 2 ? VariantTile{256, 1}
+                      : v == 3 ? VariantTile{124, 1} : v == 4 ? VariantTile{252, 1} : VariantTile{0, 0})
          : ndim == 3 ? (v == 0 ? VariantTile{32, 8} : v == 1 ? VariantTile{32, 16} : v == 2 ? VariantTile{64, 8} : VariantTile{0, 0})
                      : VariantTile{0, 0};
 }
@@ -166,6 +170,8 @@ static cudaError_t launch_multi_stage_prec(const MultiArgs &a, int ndim, int v, 
         case 20: return multi_stage_v<R, 2, 0>(a, stage, nblocks, s);
         case 21: return multi_stage_v<R, 2, 1>(a, stage, nblocks, s);
         case 22: return multi_stage_v<R, 2, 2>(a, stage, nblocks, s);
+        case 23: return multi_stage_v<R, 2, 3>(a, stage, nblocks, s);
+        case 24: return multi_stage_v<R, 2, 4>(a, stage, nblocks, s);
         case 30: return multi_stage_v<R, 3, 0>(a, stage, nblocks, s);
         case 31: return multi_stage_v<R, 3, 1>(a, stage, nblocks, s);
         case 32: return multi_stage_v<R, 3, 2>(a, stage, nblocks, s);
@@ -190,6 +196,8 @@ static int multi_resident_prec(int ndim, int v) {
         case 20: return multi_resident_v<R, 2, 0>();
         case 21: return multi_resident_v<R, 2, 1>();
         case 22: return multi_resident_v<R, 2, 2>();
+        case 23: return multi_resident_v<R, 2, 3>();
+        case 24: return multi_resident_v<R, 2, 4>();
         case 30: return multi_resident_v<R, 3, 0>();
         case 31: return multi_resident_v<R, 3, 1>();
         case 32: return multi_resident_v<R, 3, 2>();
