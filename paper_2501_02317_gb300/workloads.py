@@ -126,6 +126,21 @@ def sod(n: int = 512, axis: int = 0, ndim: int = 1, ntrans: int = 4, prec: int =
     return mesh, W
 
 
+def shock_tube(n: int, left: Sequence[float], right: Sequence[float], x0: float = 0.5, gamma: float = 1.4,
+               prec: int = PREC_FP64, cfl: float = 0.4, bc: int = BC_FREE) -> Tuple[Mesh, np.ndarray]:
+    """1D Riemann problem on [0, 1] (Sec. 4.2): primitive states (rho, v, p)
+    left and right of x0.  Zero-gradient ("free") ends by default: the
+    outflow rule of Sec. 3.1.1 refuses inflow, which would launch a wave from
+    an end where the state moves into the tube."""
+    mesh = Mesh(ndim=1, n=(n, 1, 1), gamma=gamma, cfl=cfl,
+                bc=((bc, bc), (BC_PERIODIC, BC_PERIODIC), (BC_PERIODIC, BC_PERIODIC)), prec=prec)
+    W = _empty(mesh)
+    lft = _grids(mesh)[0] < x0
+    for q in range(3):
+        W[q] = np.broadcast_to(np.where(lft, left[q], right[q]), mesh.shape[1:])
+    return mesh, W
+
+
 # ------------------------------------------------ Sec. 4.1 linear sound wave
 
 

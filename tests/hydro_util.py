@@ -41,3 +41,22 @@ def field_errors(mesh, U, Uref):
     errs = [rel_l1(U[q], Uref[q]) for q in range(mesh.nvar)]
     errs.append(rel_l1(pressure_np(mesh, U), pressure_np(mesh, Uref)))
     return errs
+
+
+# Riemann problems for the Sec. 4.2 shock-tube checks (values chosen here,
+# not a published suite): (left (rho, v, p), right, x0, t_end)
+SHOCK_TUBES = {
+    "strong_shock": ((1.0, 0.0, 500.0), (1.0, 0.0, 0.02), 0.5, 0.012),
+    "double_rarefaction": ((1.0, -1.8, 0.5), (1.0, 1.8, 0.5), 0.5, 0.12),
+    "colliding_streams": ((1.2, 2.4, 1.5), (0.9, -2.1, 0.9), 0.5, 0.06),
+    "moving_contact": ((1.3, 0.15, 1.0), (0.8, 0.15, 1.0), 0.5, 0.5),
+    "shock_into_rest": ((2.5, 1.2, 4.0), (1.0, 0.0, 1.0), 0.4, 0.08),
+}
+
+
+def tube_errors(left, right, x0, t, gamma, W):
+    """Mean |W - exact cell average| per primitive, over max |exact|."""
+    from oracle import exact_riemann as er
+    n = W.shape[-1]
+    ex = er.cell_averages(left, right, gamma, x0, t, np.linspace(0.0, 1.0, n + 1))
+    return [float(np.mean(np.abs(W[q].ravel() - ex[q]))) / float(np.abs(ex[q]).max()) for q in range(3)]

@@ -1,0 +1,60 @@
+"""The CUDA path on the shock tubes beyond Sod (Sec. 4.2), through the C ABI:
+the all-FP64 path equals the oracle bit for bit; the mixed and FP32 paths
+follow the exact solution within the oracle's own error bounds, and the
+mixed path stays within the per-field gates of the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from hydro_util import SHOCK_TUBES, field_errors, gpu_run, tube_errors
+from paper_2501_02317_gb300 import workloads as wl
+from test_oracle_shock_tubes import BOUNDS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2501_02317_gb300 import build as kbuild
+    from paper_2501_02317_gb300 import khydro
+    kbuild.build()
+    khydro.lib()
+    oracle.set_threads(0)
+
+
+def _case(name, prec):
+    left, right, x0, t = SHOCK_TUBES[name]
+    mesh, W = wl.shock_tube(512, left, right, x0, prec=prec)
+    return mesh, W, left, right, x0, t
+
+
+@pytest.mark.parametrize("name", sorted(SHOCK_TUBES))
+def test_fp64_equals_oracle_bitwise(name):
+    mesh, W, _, _, _, t = _case(name, wl.PREC_FP64)
+    Uo, to, so, fo = oracle.run(mesh, oracle.prim_to_cons(mesh, W), 0.0, t)
+    U, tg, sg, _ = gpu_run(mesh, W, t)
+    assert sg == so and tg == to == t
+    np.testing.assert_array_equal(U, Uo)
+
+
+@pytest.mark.parametrize("prec", [wl.PREC_MIXED, wl.PREC_FP32])
+@pytest.mark.parametrize("name", sorted(SHOCK_TUBES))
+def test_reduced_precision_against_exact_solution(name, prec):
+    mesh, W, left, right, x0, t = _case(name, prec)
+    U, tg, _, _ = gpu_run(mesh, W, t)
+    assert tg == t
+    Wf, _ = oracle.cons_to_prim(mesh.replace(prec=wl.PREC_FP64), U)
+    errs = tube_errors(left, right, x0, t, mesh.gamma, Wf)
+    bounds = list(BOUNDS[name])
+    if name == "moving_contact":  # v and p exact up to FP32 flux rounding over ~940 steps
+        bounds[1] = bounds[2] = 1e-5 if prec == wl.PREC_FP32 else 1e-6
+    assert all(e <= b for e, b in zip(errs, bounds)), (name, prec, errs)
+
+
+@pytest.mark.parametrize("name", sorted(SHOCK_TUBES))
+def test_mixed_within_gates_of_oracle(name):
+    mesh, W, _, _, _, t = _case(name, wl.PREC_MIXED)
+    Uo, _, _, _ = oracle.run(mesh, oracle.prim_to_cons(mesh, W), 0.0, t)
+    U, _, _, _ = gpu_run(mesh, W, t)
+    errs = field_errors(mesh, U, Uo)
+    assert errs[0] <= 1e-5 and errs[-1] <= 1e-4, (name, errs)
