@@ -195,16 +195,23 @@ __device__ __forceinline__ void recover(const double (&u)[ND + 2], const MixCons
         ++floors;
     }
     const float rho32 = d2f_state(rho);
-    const float r32 = rcp_approx(rho32);  // ~1 ulp; the FP64 Newton step below squares its error
-    double r = f2d_fast(r32);
-    const double e = __fma_rn(-rho, r, 1.0);  // one Newton step: |1 - rho r| ~ 2^-46
-    r = __fma_rn(r, e, r);
+    const float r32 = rcp_approx(rho32);  // r0 ~ 1/rho to ~1 ulp of FP32
+    const float hr32 = __fmul_rn(0.5f, r32);
+    // e = 1 - rho r0 in FP64 (|e| ~ 2^-23, so 1/rho = r0 (1 + e) + O(2^-46)),
+    // then the internal energy E - |m|^2 r0 (1 + e) / 2 as the FP64 part
+    // e0 = E - |m|^2 r0 / 2 minus the small FP32 correction (|m|^2 r0 / 2) e:
+    // the cancellation between E and the kinetic energy happens in FP64, and
+    // the result carries the error of an FP64 recovery with a one-step Newton
+    // reciprocal -- a few units of 2^-24 eint + 2^-44 |m|^2 / rho -- with five
+    // FP64 operations instead of seven.
+    const float e = d2f_state(__fma_rn(-rho, f2d_fast(r32), 1.0));
     double msq = __dmul_rn(u[1], u[1]);
 #pragma unroll
     for (int d = 1; d < ND; ++d) msq = __fma_rn(u[1 + d], u[1 + d], msq);
-    const double eint = __fma_rn(-0.5, __dmul_rn(msq, r), u[ND + 1]);
-    if (negative_or_nan(eint)) flags |= FLAG_NONPHYSICAL;
-    float p = __fmul_rn(k.gm1, d2f_state(eint));
+    const double e0 = __fma_rn(f2d_fast(-hr32), msq, u[ND + 1]);
+    const float eint = __fsub_rn(d2f_state(e0), __fmul_rn(__fmul_rn(d2f_state(msq), hr32), e));
+    if (negative_or_nan(e0) || eint < 0.0f) flags |= FLAG_NONPHYSICAL;  // NaN and Inf show in e0
+    float p = __fmul_rn(k.gm1, eint);
     if (p < k.p_floor) {
         p = k.p_floor;
         flags |= FLAG_FLOOR;
