@@ -41,19 +41,28 @@ BYTES_PER_CELL_UPDATE_3D_FP32 = 100
 BYTES_PER_CELL_UPDATE_3D_VL2 = 160
 
 
+# the translation unit of the mixed stage kernels and every file it includes
+STAGE_SOURCES = ("khy_mixed.cu", "khy_launch.cuh", "khy_internal.h", "khy_stage.cuh", "khy_kernels.cuh",
+                 "khy_mixed_kernels.cuh", "khy_packed.cuh", "khy_single_kernels.cuh")
+
+
+def stage_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in STAGE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2501_02317_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def _recorded_traffic(workload: str):
     """DRAM bytes (read + write) of the stage-kernel pair from the committed
-    ncu capture, or None when the kernel sources changed since it was taken."""
-    import glob
-    import hashlib
+    ncu capture, or None when the stage kernels' sources changed since it was
+    taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "stage_traffic.json")) as f:
             rec = json.load(f)
-        h = hashlib.sha256()
-        for fn in sorted(glob.glob(os.path.join(ROOT, "paper_2501_02317_gb300", "csrc", "*"))):
-            with open(fn, "rb") as f:
-                h.update(f.read())
-        if rec.get("csrc_sha256") != h.hexdigest() or rec.get("workload") != workload:
+        if rec.get("stage_sources_sha256") != stage_sources_sha256() or rec.get("workload") != workload:
             return None
         return float(rec["stage1_dram_bytes"]) + float(rec["stage2_dram_bytes"])
     except Exception:

@@ -251,7 +251,8 @@ khy_status batch_status(const khy_batch *b) {
 namespace khy {
 // Cost model per plane of a tile run: its active cells plus a fixed part for
 // the barriers and index work; every run (and every piece of a split run)
-// also pays the four warm-up planes of the march.  Boundaries between CTAs
+// also pays a warm-up -- its first planes of stored primitives are copied and
+// the march faces below its first plane computed -- about one plane of work.  Boundaries between CTAs
 // are placed at multiples of total/nblocks of the cumulative cost; the total
 // is re-estimated after each pass because splits add warm-up planes.
 void build_segments(const std::vector<int> &ids, const std::vector<Geom> &geoms, int ndim, int TX, int TY,
@@ -259,7 +260,7 @@ void build_segments(const std::vector<int> &ids, const std::vector<Geom> &geoms,
     struct Run { int id, x0, y0, nm; double per; };
     std::vector<Run> runs;
     const double fixed = 0.25 * TX * TY;
-    const double warm = ndim >= 2 ? 4.0 : 0.0;
+    const double warm = ndim >= 2 ? 1.0 : 0.0;
     double W = 0.0;
     for (size_t i = 0; i < geoms.size(); ++i) {
         const Geom &g = geoms[i];

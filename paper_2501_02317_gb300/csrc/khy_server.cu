@@ -163,7 +163,7 @@ struct khy_server {
     int *d_slots[4] = {};
     size_t cap_segs[4] = {}, cap_cta[4] = {}, cap_slots[4] = {};
     int nblocks[4] = {}, nactive[4] = {};
-    int variant[4] = {1, 1, 3, 1};  // tile variants: 2D rows of 124, 3D 32x16
+    int variant[4] = {1, 1, 3, 0};  // tile variants: 2D rows of 124, 3D 32x8
     bool dirty[4] = {true, true, true, true};
     double *h_stage = nullptr;  // pinned staging for W / results
     size_t h_stage_len = 0;
