@@ -227,6 +227,37 @@ def bench_serving(khydro, wl, njobs: int = 60, budget_bytes: int = 16 << 30, slo
     return out
 
 
+class Ranks:
+    """Collectives of the replica harness (one process per GPU, each stepping
+    its own copy of the workload): a barrier, and the maximum of a host value
+    over ranks -- the timed region ends when the slowest rank ends.  `dist`
+    is torch.distributed after init_process_group (NCCL on GPUs, gloo in the
+    CPU tests) or None for one process."""
+
+    def __init__(self, dist=None, device: str = "cpu"):
+        self.dist = dist
+        self.device = device
+        self.world = dist.get_world_size() if dist is not None else 1
+        self.rank = dist.get_rank() if dist is not None else 0
+
+    def barrier(self) -> None:
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Units all ranks processed per second of the slowest rank (weak scaling)."""
+    return world * units_per_rank / seconds
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -284,17 +315,8 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(dist, "cuda")
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     from paper_2501_02317_gb300 import build as kbuild
     kbuild.build()
@@ -330,7 +352,7 @@ def main():
         el = timed_steps(sim, K)
     clocks = clk.summary()
     el = max_over_ranks(el)
-    value = world * ncell * K / el
+    value = whole_job_rate(world, ncell * K, el)
     flags, floors = sim.flags()
     ms = sim.profile_steps(T_END, 5)
     stage_ms = ms[1] + ms[2]
@@ -344,7 +366,7 @@ def main():
     torch.cuda.synchronize()
     k64 = max(3, K // 10)
     el64 = max_over_ranks(timed_steps(sim64, k64))
-    value64 = world * ncell * k64 / el64
+    value64 = whole_job_rate(world, ncell * k64, el64)
     ms64 = sim64.profile_steps(T_END, 2)
     sim64.close()
 
@@ -360,7 +382,7 @@ def main():
         state_bytes = s.device_bytes()[0]
         s.close()
         ach = bytes_per_cu * ncell / ((pm[1] + pm[2]) * 1e-3) / 1e9
-        return {"value": world * ncell * k / t, "unit": UNIT, "steps": k, "ms_per_step": 1e3 * t / k,
+        return {"value": whole_job_rate(world, ncell * k, t), "unit": UNIT, "steps": k, "ms_per_step": 1e3 * t / k,
                 "stage_ms": [pm[1], pm[2]], "state_bytes": state_bytes, "bytes_per_cell_update": bytes_per_cu,
                 "hbm_achieved_gbs": ach, "hbm_frac": ach / peak_gbs}
 
@@ -383,7 +405,7 @@ def main():
             sim.conserved(Uh)
         torch.cuda.synchronize()
         el_e2e = max_over_ranks(time.perf_counter() - t0)
-        e2e = {"value": world * ncell * ke / el_e2e, "unit": UNIT, "h2d_bytes_per_step": int(Uh.nbytes),
+        e2e = {"value": whole_job_rate(world, ncell * ke, el_e2e), "unit": UNIT, "h2d_bytes_per_step": int(Uh.nbytes),
                "d2h_bytes_per_step": int(Uh.nbytes), "steps": ke,
                "api": "khy_set_conserved(host) + khy_enqueue_steps(1) + khy_get_conserved(host)"}
     sim.close()
