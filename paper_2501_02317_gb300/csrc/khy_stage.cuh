@@ -169,11 +169,10 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     double dtq[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) dtq[d] = STAGE == 3 ? 0.5 * dtdx[d] : dtdx[d];
-    // dt/dx and dt/(2 dx) rounded to FP32 once (they scale the small
-    // low-order part of the flux sums in the mixed update)
+    // dt/(2 dx) for the mixed Heun average; dt/dx_d rounded to FP32 once for
+    // the all-FP32 update
     const double hcd = 0.5 * dtq[0];
-    const float c32 = mx::d2f(dtq[0]), hc32 = mx::d2f(hcd);
-    const float c32x = c32, c32y = mx::d2f(dtq[1]), c32m = mx::d2f(dtq[DM < 0 ? 0 : DM]);
+    const float c32x = mx::d2f(dtq[0]), c32y = mx::d2f(dtq[1]), c32m = mx::d2f(dtq[DM < 0 ? 0 : DM]);
 
     // tiles whose halo box lies inside the grid skip the ghost-zone index map
     const bool x_inside = x0 >= 2 && x0 + wact + 2 <= g.n[0];
