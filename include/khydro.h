@@ -50,7 +50,7 @@ typedef enum {
     KHY_ERR_CUDA = -3,         /* a CUDA runtime call failed */
     KHY_ERR_NONPHYSICAL = -4,  /* rho <= 0, E - ke < 0 or NaN seen by the recovery */
     KHY_ERR_DT_UNDERFLOW = -5, /* the CFL step fell below 1e-300 or is not finite */
-    KHY_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
+    KHY_ERR_TIMEOUT = -6,      /* a bounded wait gave up (khy_server_wait; no kernel waits on another) */
     KHY_ERR_BUDGET = -7        /* serving: the job does not fit the HBM budget */
 } khy_status;
 

@@ -60,3 +60,36 @@ def test_server_rejects_job_beyond_budget(kh):
         assert ei.value.status == -7
         with pytest.raises(kh.KhydroError):
             srv.submit(wl.sod(64)[0].replace(prec=wl.PREC_MIXED), wl.sod(64)[1], 0.1)  # 1D is not served
+
+
+def test_server_wait_times_out_then_completes(kh):
+    # a bounded host wait: KHY_ERR_TIMEOUT while the job still runs, then done
+    m, W = wl.turbulence(48, prec=wl.PREC_MIXED)
+    with kh.Server(hbm_budget_bytes=1 << 30, max_slots=4) as srv:
+        jid = srv.submit(m, W, 0.3)
+        with pytest.raises(kh.KhydroError) as ei:
+            srv.wait(jid, 1e-6)
+        assert ei.value.status == -6
+        srv.wait(jid, 600.0)
+        state, _, steps = srv.poll(jid)
+        assert steps > 0
+        np.testing.assert_array_equal(srv.result(jid), gpu_run(m, W, 0.3)[0])
+
+
+def test_server_isolates_a_failing_job(kh):
+    # a job whose state is not physical (negative pressure in a box) is
+    # reported failed; the jobs stepped with it finish exactly as alone
+    jobs = small_jobs(5, seed=7)
+    bad_m, bad_W = wl.kelvin_helmholtz(48)
+    bad_W = bad_W.copy()
+    bad_W[3, 0, 10:20, 10:20] = -1.0
+    with kh.Server(hbm_budget_bytes=1 << 30, max_slots=8) as srv:
+        ids = [srv.submit(m, W, te) for m, W, te in jobs[:2]]
+        bad = srv.submit(bad_m, bad_W, 0.05)
+        ids += [srv.submit(m, W, te) for m, W, te in jobs[2:]]
+        with pytest.raises(kh.KhydroError) as ei:
+            srv.wait(bad, 600.0)
+        assert ei.value.status == -4
+        for jid, (m, W, te) in zip(ids, jobs):
+            srv.wait(jid, 600.0)
+            np.testing.assert_array_equal(srv.result(jid), gpu_run(m, W, te)[0])
