@@ -243,9 +243,12 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
     // thread after its copies have landed (fix_plane).
     // tiles whose halo box lies inside the grid copy whole rows in 8-byte
     // pairs (the row start x0 - 2 is even, and so is every row and field
-    // offset when nx is even); the others copy cell by cell through the
-    // ghost-zone index map
-    const bool rows8 = x_inside && y_inside && (g.n[0] % 2 == 0);
+    // offset when nx is even) -- provided the grid's primitive array itself
+    // starts on 8 bytes, which a grid packed after one with an odd cell
+    // count in a many-grid pool does not; the others copy cell by cell
+    // through the ghost-zone index map
+    const bool rows8 = x_inside && y_inside && (g.n[0] % 2 == 0) &&
+                       (reinterpret_cast<unsigned long long>(Win) % 8 == 0);
     auto load_plane_async = [&](int L, int slot) {
         if constexpr (MIX && FROM_W) {
             R *dst = sW + (size_t)slot * NV * PC;

@@ -94,3 +94,26 @@ def test_batch_1d_3d_fp64_bitwise_vs_oracle(kh, ndim):
     for (m, W), U in zip(grids, res):
         Uo, _, _, _ = oracle_run(m, W, max_steps=5)
         np.testing.assert_array_equal(U, Uo)
+
+
+@pytest.mark.parametrize("ndim", [1, 3])
+def test_mixed_batch_odd_sized_grids_equal_alone(kh, ndim):
+    # grids with an odd cell count shift the next grid's primitives in the
+    # pool off 8 bytes; the even-width grids after them have interior tiles,
+    # whose 8-byte row copies apply only to an aligned array
+    sizes = {1: [(51, 1, 1), (600, 1, 1), (77, 1, 1), (512, 1, 1)],
+             3: [(45, 45, 45), (96, 24, 10), (37, 9, 11), (96, 26, 8)]}[ndim]
+    grids = []
+    for k, n in enumerate(sizes):
+        m = wl.Mesh(ndim=ndim, n=n, gamma=5.0 / 3.0, cfl=0.3, prec=wl.PREC_MIXED)
+        grids.append((m, wl.random_smooth(m, seed=k)))
+    assert any(m.ncell % 2 for m, _ in grids)
+    alone = [gpu_run(m, W, max_steps=6)[0] for m, W in grids]
+    for v in range(2 if ndim == 1 else 3):
+        with kh.Batch([m for m, _ in grids]) as b:
+            b.set_variant(v)
+            b.set_primitive([W for _, W in grids])
+            b.set_target(1e30, 6)
+            b.run()
+            for U, A in zip(b.conserved(), alone):
+                np.testing.assert_array_equal(U, A)
