@@ -241,7 +241,8 @@ khy_status khy_batch_set_variant(khy_batch *b, int variant);
  * stage-2 launches over nsteps un-graphed steps. */
 khy_status khy_batch_profile_steps(khy_batch *b, long nsteps, float ms[3]);
 
-/* Total cells, pooled doubles per state, current variant, CTAs of the schedule. */
+/* Total cells, pooled doubles per state (every grid at a 32-element offset:
+ * at least the sum of nvar*ncell), current variant, CTAs of the schedule. */
 khy_status khy_batch_info(khy_batch *b, long long *cells, size_t *pool_doubles, int *variant, int *nblocks);
 
 /* ------------------------------------------------------------ serving */

@@ -2,8 +2,9 @@
 // served workloads).
 //
 // All grids of a batch share one dimensionality and one precision.  Their
-// conserved states are concatenated in one device pool (grid i at offset
-// off_i, each grid field-major as in the single-grid API), U^1 in a second
+// conserved states share one device pool (grid i at offset off_i, a
+// multiple of 32 elements so that every grid's arrays start on 128 bytes;
+// each grid field-major as in the single-grid API), U^1 in a second
 // pool, and the primitives of U^n and U^1 in two pools of the flux precision
 // at the same offsets (the stage kernels read them instead of recovering halo
 // cells, as a single grid's Heun step does); every grid has its own clock,
@@ -56,14 +57,27 @@ __global__ void multi_wmin_reset_kernel(Clock *clocks, int ngrids) {
     if (i < ngrids) clocks[i].wmin_bits = kInfBits;
 }
 
-// primitive -> conserved for every grid (Eq. 2), one block per grid at a time
+// a state between the host layout and the pool layout, one block per grid
+__global__ void multi_relayout_kernel(const GridDesc *grids, const long long *hoff, int ngrids, int nvar,
+                                      const double *src, double *dst, int to_pool) {
+    for (int gi = blockIdx.x; gi < ngrids; gi += gridDim.x) {
+        const long long n = (long long)nvar * grids[gi].g.ncell;
+        const double *s = src + (to_pool ? hoff[gi] : grids[gi].off);
+        double *d = dst + (to_pool ? grids[gi].off : hoff[gi]);
+        for (long long c = threadIdx.x; c < n; c += blockDim.x) d[c] = s[c];
+    }
+}
+
+// primitive (host layout: grids back to back, grid i at hoff[i]) ->
+// conserved (pool layout) for every grid (Eq. 2), one block per grid at a time
 template <int ND>
-__global__ void multi_prim_to_cons_kernel(const GridDesc *grids, int ngrids, const double *W, double *U) {
+__global__ void multi_prim_to_cons_kernel(const GridDesc *grids, const long long *hoff, int ngrids,
+                                          const double *W, double *U) {
     constexpr int NV = ND + 2;
     for (int gi = blockIdx.x; gi < ngrids; gi += gridDim.x) {
         const GridDesc &gd = grids[gi];
         const long long N = gd.g.ncell;
-        const double *w = W + gd.off;
+        const double *w = W + hoff[gi];
         double *u = U + gd.off;
         for (long long c = threadIdx.x; c < N; c += blockDim.x) {
             const double rho = w[c];
@@ -110,7 +124,10 @@ struct khy_batch {
     int ngrids = 0, ndim = 0, prec = 0, nvar = 0;
     std::vector<khy_mesh_desc> desc;
     std::vector<GridDesc> gd;
-    size_t pool = 0;  // doubles per state pool
+    size_t pool = 0;   // doubles per state pool (grids at 32-element offsets)
+    size_t hpool = 0;  // doubles of a host state array (grids back to back)
+    std::vector<long long> hoff;      // grid offsets in a host state array
+    long long *d_hoff = nullptr;
     long long cells = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -369,12 +386,16 @@ khy_status khy_batch_create(const khy_mesh_desc *descs, int ngrids, void *cuda_s
     b->nvar = 2 + b->ndim;
     b->desc.assign(descs, descs + ngrids);
     b->gd.resize(ngrids);
-    size_t off = 0;
+    size_t off = 0, hoff = 0;
+    b->hoff.resize(ngrids);
     for (int i = 0; i < ngrids; ++i) {
         GridDesc &g = b->gd[i];
         memset(&g, 0, sizeof(g));
         g.g = geom_of_desc(descs[i]);
+        off = (off + 31) & ~size_t(31);
         g.off = (long long)off;
+        b->hoff[i] = (long long)hoff;
+        hoff += (size_t)b->nvar * (size_t)g.g.ncell;
         g.cubic = 1;
         for (int d = 1; d < b->ndim; ++d)
             if (g.g.dx[d] != g.g.dx[0]) g.cubic = 0;
@@ -382,6 +403,7 @@ khy_status khy_batch_create(const khy_mesh_desc *descs, int ngrids, void *cuda_s
         b->cells += g.g.ncell;
     }
     b->pool = off;
+    b->hpool = hoff;
     cudaError_t e = cudaSuccess;
     if (cuda_stream) b->stream = (cudaStream_t)cuda_stream;
     else {
@@ -394,6 +416,9 @@ khy_status khy_batch_create(const khy_mesh_desc *descs, int ngrids, void *cuda_s
     if (e == cudaSuccess) e = cudaMalloc(&b->W0, wsize * b->pool);
     if (e == cudaSuccess) e = cudaMalloc(&b->W1, wsize * b->pool);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, sizeof(GridDesc) * ngrids);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_hoff, sizeof(long long) * ngrids);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_hoff, b->hoff.data(), sizeof(long long) * ngrids, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_clocks, sizeof(Clock) * ngrids);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_clocks, sizeof(Clock) * ngrids);
     if (e == cudaSuccess) {
@@ -435,6 +460,7 @@ void khy_batch_destroy(khy_batch *b) {
     cudaFree(b->W0);
     cudaFree(b->W1);
     cudaFree(b->d_grids);
+    cudaFree(b->d_hoff);
     cudaFree(b->d_clocks);
     cudaFree(b->d_segs);
     cudaFree(b->d_cta);
@@ -445,13 +471,13 @@ void khy_batch_destroy(khy_batch *b) {
 
 khy_status khy_batch_set_primitive(khy_batch *b, const double *W, size_t count) {
     if (!b || !W) return bfail(KHY_ERR_ARG, "khy_batch_set_primitive: NULL argument");
-    if (count != b->pool) return bfail(KHY_ERR_ARG, "khy_batch_set_primitive: count must be the sum of nvar*ncell");
+    if (count != b->hpool) return bfail(KHY_ERR_ARG, "khy_batch_set_primitive: count must be the sum of nvar*ncell");
     KHY_BCUDA(cudaMemcpyAsync(b->U1, W, sizeof(double) * count, cudaMemcpyHostToDevice, b->stream));
     const int blocks = std::min(b->ngrids, 152 * 8);
     switch (b->ndim) {
-        case 1: multi_prim_to_cons_kernel<1><<<blocks, 256, 0, b->stream>>>(b->d_grids, b->ngrids, b->U1, b->U); break;
-        case 2: multi_prim_to_cons_kernel<2><<<blocks, 256, 0, b->stream>>>(b->d_grids, b->ngrids, b->U1, b->U); break;
-        default: multi_prim_to_cons_kernel<3><<<blocks, 256, 0, b->stream>>>(b->d_grids, b->ngrids, b->U1, b->U); break;
+        case 1: multi_prim_to_cons_kernel<1><<<blocks, 256, 0, b->stream>>>(b->d_grids, b->d_hoff, b->ngrids, b->U1, b->U); break;
+        case 2: multi_prim_to_cons_kernel<2><<<blocks, 256, 0, b->stream>>>(b->d_grids, b->d_hoff, b->ngrids, b->U1, b->U); break;
+        default: multi_prim_to_cons_kernel<3><<<blocks, 256, 0, b->stream>>>(b->d_grids, b->d_hoff, b->ngrids, b->U1, b->U); break;
     }
     KHY_BCUDA(cudaGetLastError());
     KHY_BCUDA(cudaStreamSynchronize(b->stream));
@@ -461,8 +487,11 @@ khy_status khy_batch_set_primitive(khy_batch *b, const double *W, size_t count) 
 
 khy_status khy_batch_set_conserved(khy_batch *b, const double *U, size_t count) {
     if (!b || !U) return bfail(KHY_ERR_ARG, "khy_batch_set_conserved: NULL argument");
-    if (count != b->pool) return bfail(KHY_ERR_ARG, "khy_batch_set_conserved: count must be the sum of nvar*ncell");
-    KHY_BCUDA(cudaMemcpyAsync(b->U, U, sizeof(double) * count, cudaMemcpyHostToDevice, b->stream));
+    if (count != b->hpool) return bfail(KHY_ERR_ARG, "khy_batch_set_conserved: count must be the sum of nvar*ncell");
+    KHY_BCUDA(cudaMemcpyAsync(b->U1, U, sizeof(double) * count, cudaMemcpyHostToDevice, b->stream));  // staging
+    multi_relayout_kernel<<<std::min(b->ngrids, 152 * 8), 256, 0, b->stream>>>(b->d_grids, b->d_hoff, b->ngrids,
+                                                                                b->nvar, b->U1, b->U, 1);
+    KHY_BCUDA(cudaGetLastError());
     KHY_BCUDA(cudaStreamSynchronize(b->stream));
     b->wmin_valid = false;
     return KHY_OK;
@@ -470,8 +499,12 @@ khy_status khy_batch_set_conserved(khy_batch *b, const double *U, size_t count) 
 
 khy_status khy_batch_get_conserved(khy_batch *b, double *U, size_t count) {
     if (!b || !U) return bfail(KHY_ERR_ARG, "khy_batch_get_conserved: NULL argument");
-    if (count != b->pool) return bfail(KHY_ERR_ARG, "khy_batch_get_conserved: count must be the sum of nvar*ncell");
-    KHY_BCUDA(cudaMemcpyAsync(U, b->U, sizeof(double) * count, cudaMemcpyDeviceToHost, b->stream));
+    if (count != b->hpool) return bfail(KHY_ERR_ARG, "khy_batch_get_conserved: count must be the sum of nvar*ncell");
+    // U1 holds nothing between steps: it stages the host layout
+    multi_relayout_kernel<<<std::min(b->ngrids, 152 * 8), 256, 0, b->stream>>>(b->d_grids, b->d_hoff, b->ngrids,
+                                                                                b->nvar, b->U, b->U1, 0);
+    KHY_BCUDA(cudaGetLastError());
+    KHY_BCUDA(cudaMemcpyAsync(U, b->U1, sizeof(double) * count, cudaMemcpyDeviceToHost, b->stream));
     KHY_BCUDA(cudaStreamSynchronize(b->stream));
     return KHY_OK;
 }

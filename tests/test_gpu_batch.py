@@ -98,9 +98,9 @@ def test_batch_1d_3d_fp64_bitwise_vs_oracle(kh, ndim):
 
 @pytest.mark.parametrize("ndim", [1, 3])
 def test_mixed_batch_odd_sized_grids_equal_alone(kh, ndim):
-    # grids with an odd cell count shift the next grid's primitives in the
-    # pool off 8 bytes; the even-width grids after them have interior tiles,
-    # whose 8-byte row copies apply only to an aligned array
+    # grids with odd cell counts ahead of even-width grids with interior
+    # tiles (8-byte row copies): the pool keeps every grid at a 32-element
+    # offset while the host arrays stay back to back
     sizes = {1: [(51, 1, 1), (600, 1, 1), (77, 1, 1), (512, 1, 1)],
              3: [(45, 45, 45), (96, 24, 10), (37, 9, 11), (96, 26, 8)]}[ndim]
     grids = []
