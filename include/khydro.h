@@ -298,7 +298,8 @@ khy_status khy_server_stats(khy_server *s, long *completed, int *active, int *qu
 
 /* Capacity, in bytes, of the stage-1 scratch state that khy_step_noalloc
  * keeps in a file-scope device array: it steps meshes with
- * nvar * ncell * 8 <= KHY_NOALLOC_SCRATCH_BYTES (e.g. 1024^2 in 2D, 96^3 in 3D). */
+ * nvar * ncell * 8 <= KHY_NOALLOC_SCRATCH_BYTES (e.g. up to 1024^2 cells in
+ * 2D, exactly at the limit, or 94^3 in 3D; 95^3 is refused). */
 #define KHY_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 
 /* One Heun step that allocates nothing (the paper has no counterpart: this
@@ -313,7 +314,10 @@ khy_status khy_server_stats(khy_server *s, long *completed, int *active, int *qu
  * as one step of khy_step_to: dt from the CFL condition on U_dev, clipped so
  * the step lands on t_end; no step when t >= t_end.  Writes three doubles to
  * the device buffer out_dev: the new time, the dt taken (0 if none) and the
- * status bits (1 = non-physical state seen, 2 = a floor was applied).
+ * status bits (1 = non-physical state seen, 2 = a floor was applied, 4 = the
+ * CFL step (or the remaining t_end - t) was below 1e-300 or not finite: no
+ * step was taken, the state and time are unchanged, and a caller that loops
+ * until t_end must stop on this bit instead of calling again).
  * Stream-ordered on cuda_stream (may be NULL), no host synchronisation.
  *
  * Scratch: U^1 and the step clock live in one file-scope __device__ array of
@@ -321,7 +325,10 @@ khy_status khy_server_stats(khy_server *s, long *completed, int *active, int *qu
  * holds until the process exits; no cudaMalloc, cudaFree or allocating
  * library routine is called.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call shares the
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process: it assumes the device's primary context is not
+ * destroyed and re-created meanwhile (no cudaDeviceReset while the library
+ * is in use).  Every call shares the
  * array: calls whose work overlaps on the GPU (other streams or threads)
  * race.  Errors: KHY_ERR_ARG for an invalid descriptor, KHY_PREC_FP32,
  * KHY_INT_VL2, NULL pointers, NaN times, or a state larger than the scratch (the message gives

@@ -6,14 +6,17 @@
 //   * FP64 <-> FP32 conversions are done with integer instructions (the
 //     hardware conversions issue on the FP64 pipe).
 //   * Primitive recovery (Sec. 3.1) keeps the cancellation-prone internal
-//     energy E - |m|^2/(2 rho) in FP64 (7 FP64 operations in 3D: a Newton step
-//     on an FP32 reciprocal seed, |m|^2, and one fused multiply-add); the
+//     energy E - |m|^2/(2 rho) in FP64 (5 FP64 operations in 3D: the Newton
+//     residual e = 1 - rho r0 of an FP32 reciprocal seed r0, |m|^2 in three,
+//     and e0 = E - |m|^2 r0 / 2 in one fused multiply-add; the Newton term
+//     (|m|^2 r0 / 2) e is applied in FP32 after the cancellation); the
 //     density, velocities and the pressure leave it as FP32 primitives.
 //   * Flux differences: per cell and field, the six FP32 face fluxes are
-//     summed error-free as a float-float pair (Knuth TwoSum), so the FP64
-//     update U + c (S_hi + S_lo) costs two FP64 operations in stage 1 and
-//     three in stage 2 (the Heun average), and each face flux still enters
-//     its two cells with opposite signs to full FP64 precision.
+//     summed error-free as a float-float pair (Knuth TwoSum), the pair is
+//     turned into one double with integer operations, and the FP64 update
+//     costs one fused multiply-add per field (U + c S, or the Heun average
+//     V + (c/2) S from the stored V = (Un + U1)/2); each face flux still
+//     enters its two cells with opposite signs to full FP64 precision.
 //   * The CFL minimum for the next step is taken in FP32 from the recovered
 //     primitives of the new state.
 //

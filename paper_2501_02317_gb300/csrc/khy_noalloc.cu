@@ -12,7 +12,10 @@
 //
 // The array's name is only a host-side stand-in in host code, so its device
 // address is fetched once per device with cudaGetSymbolAddress (with that
-// device current) and passed to the kernels.  All calls share the array and
+// device current) and passed to the kernels.  The cached address is valid
+// while the device's primary context lives: a cudaDeviceReset would reload
+// the module and leave it stale, so callers must not reset the device while
+// they use this entry point.  All calls share the array and
 // it keeps the last call's contents: the clock is re-initialised at the start
 // of every call, and U1 is fully rewritten by stage 1 before stage 2 reads it.
 // Calls whose work overlaps on the GPU (different streams, or several host

@@ -27,6 +27,10 @@ STATUS_NAMES = {0: "KHY_OK", -1: "KHY_ERR_ARG", -2: "KHY_ERR_OOM", -3: "KHY_ERR_
                 -4: "KHY_ERR_NONPHYSICAL", -5: "KHY_ERR_DT_UNDERFLOW", -6: "KHY_ERR_TIMEOUT",
                 -7: "KHY_ERR_BUDGET"}
 
+# capacity of khy_step_noalloc's fixed scratch state (KHY_NOALLOC_SCRATCH_BYTES
+# of include/khydro.h; a CPU test checks that the two agree)
+KHY_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
+
 # public symbols of include/khydro.h (checked by the CPU tests)
 EXPORTS = [
     "khy_create", "khy_destroy", "khy_set_boundary", "khy_set_conserved", "khy_set_primitive",

@@ -89,3 +89,21 @@ def test_desc_struct_layout_matches_header():
     assert d.bc.offset == 84 and d.integrator.offset == 108
     assert d.rho_floor.offset == 112 and d.p_floor.offset == 120
     assert ctypes.sizeof(d) == 128
+
+
+def test_noalloc_scratch_limit_refused_on_the_host(L):
+    # the size check of khy_step_noalloc runs before any CUDA call: meshes
+    # one cell row or layer beyond the fixed scratch are refused with
+    # KHY_ERR_ARG (the pointers are never touched on this path)
+    src = open(os.path.join(ROOT, "include", "khydro.h")).read()
+    m = re.search(r"#define KHY_NOALLOC_SCRATCH_BYTES \((\d+)u \* (\d+)u \* (\d+)u\)", src)
+    assert m and int(m.group(1)) * int(m.group(2)) * int(m.group(3)) == khydro.KHY_NOALLOC_SCRATCH_BYTES
+    for n in ((1024, 1025, 1), (95, 95, 95), (96, 96, 96)):
+        mesh = wl.Mesh(ndim=2 if n[2] == 1 else 3, n=n, prec=wl.PREC_MIXED)
+        assert mesh.nvar * mesh.ncell * 8 > khydro.KHY_NOALLOC_SCRATCH_BYTES
+        with pytest.raises(khydro.KhydroError) as ei:
+            khydro.khy_step_noalloc(mesh, 16, 0.0, 1.0, 16)
+        assert ei.value.status == -1 and "no-allocation limit" in str(ei.value)
+    for n in ((1024, 1024, 1), (94, 94, 94)):  # at or under the limit
+        mesh = wl.Mesh(ndim=2 if n[2] == 1 else 3, n=n, prec=wl.PREC_MIXED)
+        assert mesh.nvar * mesh.ncell * 8 <= khydro.KHY_NOALLOC_SCRATCH_BYTES

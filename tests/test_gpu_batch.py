@@ -5,7 +5,7 @@ parity gates."""
 import numpy as np
 import pytest
 
-from hydro_util import field_errors, gpu_run, oracle_run
+from hydro_util import check_fields, gpu_run, oracle_run
 from paper_2501_02317_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -56,8 +56,7 @@ def test_batch_against_oracle(kh):
         res = b.conserved()
     for (m, W), U in zip(grids, res):
         Uo, _, so, _ = oracle_run(m, W, max_steps=10)
-        errs = field_errors(m, U, Uo)
-        assert errs[0] <= 1e-5 and errs[-1] <= 1e-4, errs
+        check_fields(m, U, Uo, False)
 
 
 def test_batch_per_grid_targets_and_autotune(kh):

@@ -1,0 +1,176 @@
+"""Parity at the workloads' full sizes and stated horizons.
+
+* 3D turbulence box 256^3 (gamma 5/3, periodic, CFL 0.3), 100 Heun steps:
+  the all-FP64 path bit for bit and the mixed path within its gates against
+  the FP64 oracle, every conserved field and the pressure; the conserved
+  totals logged after every one of the 100 steps, computed both by the
+  library's compensated sums and by the oracle's, and the drift between
+  consecutive steps within 1e-14 of sum |q| (Sec. 3.2.2: the FP64 state and
+  flux-difference accumulation keep the totals to machine accuracy).
+* 2D Kelvin-Helmholtz 1024^2 to t = 0.05 (the prefix of the t = 1 run on
+  which the mixed gate is stated; later the shear layer's instability
+  amplifies rounding differences without bound).
+* The 4096-grid blast batch (sides log-uniform in [32, 256]) stepped 200
+  times in one launch per stage with the autotuned tile variant: a seeded
+  sample of 64 grids against the oracle.
+
+Gates (hydro_util.check_fields): the all-FP64 path within 1e-12 relative L1
+in every conserved field and the pressure (in practice bit for bit); the
+mixed path within 1e-5 in density, momenta and energy and 1e-4 in pressure
+(momentum errors relative to the reference momentum magnitude).  The plain
+relative L1 of every field is logged beside the gates.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from hydro_util import check_fields, gate_errors, mixed_gates
+from paper_2501_02317_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+DRIFT_TOL = 1e-14
+TOTALS_AGREE_TOL = 1e-15
+
+
+def _log(name, payload):
+    """Per-field errors and conservation logs, printed (pytest -s shows them)
+    and written under $KHY_PARITY_LOG_DIR when that is set."""
+    print("\n%s: %s" % (name, json.dumps({k: v for k, v in payload.items() if k != "per_step"})))
+    d = os.environ.get("KHY_PARITY_LOG_DIR")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, name + ".json"), "w") as f:
+            json.dump(payload, f, indent=1)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2501_02317_gb300 import build as kbuild
+    from paper_2501_02317_gb300 import khydro
+    kbuild.build()
+    khydro.lib()
+    oracle.set_threads(0)
+    return khydro
+
+
+# ------------------------------------------------------------ 3D turbulence 256^3, 100 steps
+
+TURB_STEPS = 100
+
+
+@pytest.fixture(scope="module")
+def turb256_oracle():
+    mesh, W = wl.turbulence(256, prec=wl.PREC_FP64)
+    U0 = oracle.prim_to_cons(mesh, W)
+    U, t, s, f = oracle.run(mesh, U0, 0.0, 1e30, TURB_STEPS)
+    assert s == TURB_STEPS and f == 0
+    return W, U, t
+
+
+@pytest.mark.parametrize("prec", [wl.PREC_MIXED, wl.PREC_FP64])
+def test_turbulence_256_100_steps_with_totals_every_step(lib, turb256_oracle, prec):
+    W, Uo, to = turb256_oracle
+    mesh, _ = wl.turbulence(256, prec=prec)
+    nv = mesh.nvar
+    U = np.empty(mesh.shape)
+    drift_max = np.zeros(nv)
+    log = []
+    with lib.Sim(mesh) as sim:
+        sim.set_primitive(W)
+        sim.conserved(U)
+        scale = np.abs(U).reshape(nv, -1).sum(axis=1)
+        prev = oracle.totals(mesh, U)
+        agree_max = np.abs(sim.totals() - prev) / scale
+        for step in range(1, TURB_STEPS + 1):
+            s, _ = sim.step_to(1e30, 1)
+            assert s == 1
+            sim.conserved(U)
+            ref = oracle.totals(mesh, U)
+            # the library's compensated totals are those of the state it holds
+            agree = np.abs(sim.totals() - ref) / scale
+            drift = np.abs(ref - prev) / scale
+            agree_max = np.maximum(agree_max, agree)
+            drift_max = np.maximum(drift_max, drift)
+            log.append({"step": step, "totals": ref.tolist(), "drift": drift.tolist()})
+            assert np.all(agree <= TOTALS_AGREE_TOL), (step, agree)
+            assert np.all(drift <= DRIFT_TOL), (step, drift)
+            prev = ref
+            scale = np.abs(U).reshape(nv, -1).sum(axis=1)
+        t, steps, _ = sim.time()
+        flags, floors = sim.flags()
+    assert steps == TURB_STEPS and flags == 0 and floors == 0
+    if prec == wl.PREC_FP64:
+        assert t == to
+        np.testing.assert_array_equal(U, Uo)
+    errs = check_fields(mesh, U, Uo, prec == wl.PREC_FP64)
+    _log("turbulence256_%s" % ("fp64" if prec == wl.PREC_FP64 else "mixed"),
+         {"steps": TURB_STEPS, "rel_l1": errs, "max_drift_per_step": drift_max.tolist(),
+          "max_totals_disagreement": agree_max.tolist(), "per_step": log})
+
+
+# ------------------------------------------------------------ 2D Kelvin-Helmholtz 1024^2 to t = 0.05
+
+KH_T = 0.05
+
+
+@pytest.fixture(scope="module")
+def kh1024_oracle():
+    mesh, W = wl.kelvin_helmholtz(1024, prec=wl.PREC_FP64)
+    U, t, s, f = oracle.run(mesh, oracle.prim_to_cons(mesh, W), 0.0, KH_T)
+    assert t == KH_T and f == 0
+    return W, U, s
+
+
+@pytest.mark.parametrize("prec", [wl.PREC_MIXED, wl.PREC_FP64])
+def test_kelvin_helmholtz_1024_to_t005(lib, kh1024_oracle, prec):
+    W, Uo, so = kh1024_oracle
+    mesh, _ = wl.kelvin_helmholtz(1024, prec=prec)
+    with lib.Sim(mesh) as sim:
+        sim.set_primitive(W)
+        s, t = sim.step_to(KH_T)
+        U = sim.conserved()
+        flags, floors = sim.flags()
+    assert t == KH_T and flags == 0 and floors == 0
+    if prec == wl.PREC_FP64:
+        assert s == so
+        np.testing.assert_array_equal(U, Uo)
+    errs = check_fields(mesh, U, Uo, prec == wl.PREC_FP64)
+    _log("kh1024_t005_%s" % ("fp64" if prec == wl.PREC_FP64 else "mixed"),
+         {"t": KH_T, "steps": s, "oracle_steps": so, "rel_l1": errs})
+
+
+# ------------------------------------------------------------ 4096-grid batch, 64-grid sample
+
+BATCH_STEPS = 200
+
+
+def test_batch_4096_sample_of_64_against_oracle(lib):
+    grids = wl.batch_blasts(4096)
+    meshes = [m for m, _ in grids]
+    with lib.Batch(meshes) as b:
+        b.set_primitive([W for _, W in grids])
+        variant, _ = b.autotune(2)  # leaves state and clocks untouched
+        b.set_target(1e30, BATCH_STEPS)
+        b.run()
+        sample = np.sort(np.random.default_rng(5).choice(len(grids), size=64, replace=False))
+        res = b.conserved()
+        clocks = [b.clock(int(k)) for k in sample]
+    worst = None
+    for k, (t, s, _) in zip(sample, clocks):
+        m, W = grids[k]
+        assert s == BATCH_STEPS
+        Uo, to, so, fo = oracle.run(m, oracle.prim_to_cons(m, W), 0.0, 1e30, BATCH_STEPS)
+        assert so == BATCH_STEPS and fo == 0
+        errs = check_fields(m, res[k], Uo, False)
+        # time agrees to the FP32 CFL estimate's rounding
+        assert abs(t - to) <= 1e-5 * to
+        cur = max(e / g for e, g in zip(gate_errors(m, res[k], Uo), mixed_gates(m.nvar)))
+        if worst is None or cur > worst[0]:
+            worst = (cur, int(k), m.n[0], errs)
+    _log("batch4096_sample64", {"variant": variant, "steps": BATCH_STEPS, "sample": sample.tolist(),
+                                "worst_fraction_of_gate": worst[0], "worst_grid": worst[1],
+                                "worst_side": worst[2], "worst_rel_l1": worst[3]})

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from hydro_util import SHOCK_TUBES, field_errors, gpu_run, tube_errors
+from hydro_util import SHOCK_TUBES, check_fields, gpu_run, tube_errors
 from paper_2501_02317_gb300 import workloads as wl
 from test_oracle_shock_tubes import BOUNDS
 
@@ -56,5 +56,4 @@ def test_mixed_within_gates_of_oracle(name):
     mesh, W, _, _, _, t = _case(name, wl.PREC_MIXED)
     Uo, _, _, _ = oracle.run(mesh, oracle.prim_to_cons(mesh, W), 0.0, t)
     U, _, _, _ = gpu_run(mesh, W, t)
-    errs = field_errors(mesh, U, Uo)
-    assert errs[0] <= 1e-5 and errs[-1] <= 1e-4, (name, errs)
+    check_fields(mesh, U, Uo, False)
