@@ -166,6 +166,17 @@ khy_status khy_get_conserved(khy_sim *sim, double *U, size_t count);
 /* Stream-ordered copy of the conserved state to device memory U_dev. */
 khy_status khy_get_conserved_dev(khy_sim *sim, double *U_dev, size_t count);
 
+/* Copies the primitive state (rho, v_1..v_ndim, p) of the current conserved
+ * state to host W (count = nvar*ncell doubles, field-major like U), as the
+ * library recovers it for the fluxes (Sec. 3.1): floors applied to the
+ * primitives, values in the flux precision (FP32 in the mixed and all-FP32
+ * paths, widened to double on the host; FP64 in the all-FP64 path).  Works
+ * for every integrator (the Heun step's stored primitives, otherwise a
+ * recovery pass into the step's scratch buffer between steps).
+ * Synchronises.  Errors: KHY_ERR_ARG (NULL, wrong count), KHY_ERR_CUDA; a
+ * non-physical state is flagged as by a step (khy_get_flags). */
+khy_status khy_get_primitive(khy_sim *sim, double *W, size_t count);
+
 /* Current time, steps taken since creation and the last dt.  Synchronises. */
 khy_status khy_get_time(khy_sim *sim, double *t, long *steps, double *last_dt);
 

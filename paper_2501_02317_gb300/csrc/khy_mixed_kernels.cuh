@@ -6,11 +6,12 @@
 //   * FP64 <-> FP32 conversions are done with integer instructions (the
 //     hardware conversions issue on the FP64 pipe).
 //   * Primitive recovery (Sec. 3.1) keeps the cancellation-prone internal
-//     energy E - |m|^2/(2 rho) in FP64 (5 FP64 operations in 3D: the Newton
-//     residual e = 1 - rho r0 of an FP32 reciprocal seed r0, |m|^2 in three,
-//     and e0 = E - |m|^2 r0 / 2 in one fused multiply-add; the Newton term
-//     (|m|^2 r0 / 2) e is applied in FP32 after the cancellation); the
-//     density, velocities and the pressure leave it as FP32 primitives.
+//     energy E - |m|^2/(2 rho) at FP64 accuracy without FP64 instructions:
+//     the FP64 conserved values are split into FP32 pairs with integer
+//     operations, |m|^2 and the kinetic energy are formed as pairs from
+//     exact FMA errors and an error-free sum, and the cancelling difference
+//     is exact (Sterbenz); the density, velocities and the pressure leave it
+//     as FP32 primitives.
 //   * Flux differences: per cell and field, the six FP32 face fluxes are
 //     summed error-free as a float-float pair (Knuth TwoSum), the pair is
 //     turned into one double with integer operations, and the FP64 update
@@ -29,19 +30,6 @@ namespace khy {
 namespace mx {
 
 // ---------------------------------------------------------------- conversions
-// double -> float for the primitives of a finite state: round to nearest
-// (ties away from zero), results below the float normal range flush to zero;
-// |x| must stay below 2^128 (a non-finite or huge state is flagged by the
-// FP64 checks of the recovery).  Seven integer operations.
-__device__ __forceinline__ float d2f_state(double x) {
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const unsigned a = hi & 0x7FFFFFFFu;
-    // exponent re-bias 1023 -> 127 on the high word, then 20 + 3 mantissa bits
-    unsigned f = __funnelshift_l(lo, a - 0x38000000u, 3);
-    f += (lo >> 28) & 1u;  // the first dropped bit rounds (a carry may reach the exponent)
-    return __uint_as_float((a < 0x38100000u ? 0u : f) | (hi & 0x80000000u));
-}
-
 // double -> float, round to nearest even; results below the float normal
 // range flush to zero, above it become +-inf; NaN stays NaN.
 __device__ __forceinline__ float d2f(double x) {
@@ -155,12 +143,34 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
     return {hi, __fsub_rn(e, __fsub_rn(hi, s.hi))};
 }
 
+// FP64 value -> pair of FP32 values with integer operations only: hi is x
+// truncated to FP32's 24 significant bits, lo holds the next 23 bits, so
+// x = hi + lo + d with |d| < 2^-46 |x| (hi and lo carry x's sign; |lo| <
+// ulp(hi)).  |x| below 2^-126 gives hi = lo = 0 and below 2^-103 lo = 0;
+// |x| must stay below 2^128 -- the recovery flags larger and non-finite
+// states before it uses the pair.
+__device__ __forceinline__ FF split_d(double x) {
+    const unsigned H = (unsigned)__double2hiint(x), L = (unsigned)__double2loint(x);
+    const unsigned sgn = H & 0x80000000u, a = H & 0x7FFFFFFFu;
+    // exponent re-bias 1023 -> 127 on the high word, then 20 + 3 mantissa bits
+    const unsigned fh = __funnelshift_l(L, a - 0x38000000u, 3);
+    const float hi = __uint_as_float((a < 0x38100000u ? 0u : fh) | sgn);
+    // the 29 bits below hi: their top 23 as a float in [0, 1) (exact
+    // subtraction of the implicit one), scaled by 2^(e - 1046), e the
+    // biased FP64 exponent
+    const float f = __fsub_rn(__uint_as_float(0x3F800000u | ((L >> 6) & 0x7FFFFFu)), 1.0f);
+    const int eb = (int)(a >> 20) - 919;
+    const float sc = __uint_as_float(((unsigned)max(eb, 0) << 23) | sgn);
+    return {hi, __fmul_rn(f, sc)};
+}
+
 // ---------------------------------------------------------------- constants
 struct MixConsts {
     float gamma, gm1, g1, gp1, gm1_gp1;
     float rho_floor, p_floor;
     long long rho_floor_bits;
     double rho_floor_d;
+    float rho_floor_hi, rho_floor_lo;  // the FP64 density floor as an FP32 pair (split_d)
     float dx[3];
 };
 
@@ -171,49 +181,74 @@ __device__ __forceinline__ MixConsts make_mix(const Geom &g) {
     k.rho_floor = g.f_rho_floor; k.p_floor = g.f_p_floor;
     k.rho_floor_d = g.rho_floor;
     k.rho_floor_bits = __double_as_longlong(g.rho_floor);
+    const FF fl = split_d(g.rho_floor);
+    k.rho_floor_hi = fl.hi;
+    k.rho_floor_lo = fl.lo;
     k.dx[0] = g.f_dx[0]; k.dx[1] = g.f_dx[1]; k.dx[2] = g.f_dx[2];
     return k;
 }
 
-__device__ __forceinline__ bool nonpositive_or_nan(double x) {
-    const long long b = __double_as_longlong(x);
-    return b <= 0 || b > 0x7FF0000000000000LL;  // sign set (or +0) or NaN
-}
-
-__device__ __forceinline__ bool negative_or_nan(double x) {
-    const long long b = __double_as_longlong(x);
-    return (b < 0 && b != (long long)0x8000000000000000ull) || (b & 0x7FFFFFFFFFFFFFFFLL) > 0x7FF0000000000000LL;
-}
-
 // ---------------------------------------------------------------- Sec. 3.1
-// Conserved (FP64) -> primitive (FP32) with the internal energy in FP64.
+// Conserved (FP64) -> primitive (FP32), with the internal energy
+// E - |m|^2 / (2 rho) at FP64 accuracy and no FP64 instruction: every
+// conserved value is split exactly enough into an FP32 pair (split_d,
+// 2^-46), |m|^2 is formed as a pair from the exact errors of the squares
+// (FMA) and an error-free sum, 1/rho is the special-function reciprocal r0
+// with its Newton residual e = 1 - rho r0 applied to the kinetic energy, and
+// E - ke is taken with its leading difference exact (where the two cancel
+// they are within a factor of two: Sterbenz' lemma).  The internal energy
+// carries a few units of 2^-24 eint + 2^-44 |m|^2 / rho, the error of an
+// FP64 recovery with a one-step Newton reciprocal.  Floors on the primitive
+// only; the density floor is compared on the FP64 value.
 template <int ND>
 __device__ __forceinline__ void recover(const double (&u)[ND + 2], const MixConsts &k, float (&w)[ND + 2],
                                         unsigned &flags, unsigned &floors) {
-    double rho = u[0];
-    if (nonpositive_or_nan(rho)) flags |= FLAG_NONPHYSICAL;
-    if (__double_as_longlong(rho) < k.rho_floor_bits) {  // positive doubles order like their bits
-        rho = k.rho_floor_d;
+    FF s[ND + 2];
+    unsigned amax = 0u;
+#pragma unroll
+    for (int q = 0; q < ND + 2; ++q) {
+        s[q] = split_d(u[q]);
+        amax = max(amax, (unsigned)__double2hiint(u[q]) & 0x7FFFFFFFu);
+    }
+    // |q| >= 2^128, Inf or NaN anywhere: not a physical state
+    if (amax >= 0x47F00000u) flags |= FLAG_NONPHYSICAL;
+    const long long rb = __double_as_longlong(u[0]);
+    if (rb <= 0) flags |= FLAG_NONPHYSICAL;  // rho <= 0 (NaN is caught above)
+    float rh = s[0].hi, rl = s[0].lo;
+    if (rb < k.rho_floor_bits) {  // positive doubles order like their bits
+        rh = k.rho_floor_hi;
+        rl = k.rho_floor_lo;
         flags |= FLAG_FLOOR;
         ++floors;
     }
-    const float rho32 = d2f_state(rho);
-    const float r32 = rcp_approx(rho32);  // r0 ~ 1/rho to ~1 ulp of FP32
-    const float hr32 = __fmul_rn(0.5f, r32);
-    // e = 1 - rho r0 in FP64 (|e| ~ 2^-23, so 1/rho = r0 (1 + e) + O(2^-46)),
-    // then the internal energy E - |m|^2 r0 (1 + e) / 2 as the FP64 part
-    // e0 = E - |m|^2 r0 / 2 minus the small FP32 correction (|m|^2 r0 / 2) e:
-    // the cancellation between E and the kinetic energy happens in FP64, and
-    // the result carries the error of an FP64 recovery with a one-step Newton
-    // reciprocal -- a few units of 2^-24 eint + 2^-44 |m|^2 / rho -- with five
-    // FP64 operations instead of seven.
-    const float e = d2f_state(__fma_rn(-rho, f2d_fast(r32), 1.0));
-    double msq = __dmul_rn(u[1], u[1]);
+    const float rho32 = __fadd_rn(rh, rl);
+    const float r0 = rcp_approx(rho32);
+    const float hr = __fmul_rn(0.5f, r0);
+    const float e = __fmaf_rn(-rl, r0, __fmaf_rn(-rh, r0, 1.0f));  // 1 - rho r0, |e| ~ 2^-22
+    // |m|^2 = Sh + Sl: the squares of the high parts with their exact errors
+    // plus the cross terms 2 m_hi m_lo (m_lo^2 < 2^-46 m^2 is dropped)
+    float Sh = 0.f, Sl = 0.f;
 #pragma unroll
-    for (int d = 1; d < ND; ++d) msq = __fma_rn(u[1 + d], u[1 + d], msq);
-    const double e0 = __fma_rn(f2d_fast(-hr32), msq, u[ND + 1]);
-    const float eint = __fsub_rn(d2f_state(e0), __fmul_rn(__fmul_rn(d2f_state(msq), hr32), e));
-    if (negative_or_nan(e0) || eint < 0.0f) flags |= FLAG_NONPHYSICAL;  // NaN and Inf show in e0
+    for (int d = 0; d < ND; ++d) {
+        const float mh = s[1 + d].hi, ml = s[1 + d].lo;
+        const float P = __fmul_rn(mh, mh);
+        const float Q = __fmaf_rn(__fmul_rn(2.f, mh), ml, __fmaf_rn(mh, mh, -P));
+        if (d == 0) {
+            Sh = P;
+            Sl = Q;
+        } else {  // TwoSum of the high parts
+            const float t = __fadd_rn(Sh, P);
+            const float bb = __fsub_rn(t, Sh);
+            const float err = __fadd_rn(__fsub_rn(Sh, __fsub_rn(t, bb)), __fsub_rn(P, bb));
+            Sh = t;
+            Sl = __fadd_rn(Sl, __fadd_rn(err, Q));
+        }
+    }
+    // ke = |m|^2 r0 (1 + e) / 2 = kh + kl
+    const float kh = __fmul_rn(Sh, hr);
+    const float kl = __fmaf_rn(kh, e, __fmaf_rn(Sl, hr, __fmaf_rn(Sh, hr, -kh)));
+    const float eint = __fadd_rn(__fsub_rn(s[ND + 1].hi, kh), __fsub_rn(s[ND + 1].lo, kl));
+    if (!(eint >= 0.0f)) flags |= FLAG_NONPHYSICAL;
     float p = __fmul_rn(k.gm1, eint);
     if (p < k.p_floor) {
         p = k.p_floor;
@@ -222,7 +257,7 @@ __device__ __forceinline__ void recover(const double (&u)[ND + 2], const MixCons
     }
     w[0] = rho32;
 #pragma unroll
-    for (int d = 0; d < ND; ++d) w[1 + d] = __fmul_rn(d2f_state(u[1 + d]), r32);
+    for (int d = 0; d < ND; ++d) w[1 + d] = __fmul_rn(__fadd_rn(s[1 + d].hi, s[1 + d].lo), r0);
     w[ND + 1] = p;
 }
 

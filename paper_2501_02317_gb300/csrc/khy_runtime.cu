@@ -629,6 +629,36 @@ khy_status khy_get_conserved(khy_sim *s, double *U, size_t count) {
     return KHY_OK;
 }
 
+khy_status khy_get_primitive(khy_sim *s, double *W, size_t count) {
+    if (!s || !W) return fail(KHY_ERR_ARG, "NULL argument");
+    khy_status st = check_count(s, count);
+    if (st != KHY_OK) return st;
+    st = ensure_wmin(s);  // Heun: the primitives of U^n are (now) in W0
+    if (st != KHY_OK) return st;
+    void *src = s->W0;
+    if (!src) {
+        // lean Heun and van Leer keep no primitives between steps: recover
+        // them into the step's scratch buffer (U1 holds nvar*ncell values of
+        // the flux precision).  The CFL minimum this pass contributes is the
+        // one already accumulated for the next step (same candidates).
+        src = s->U1;
+        const int vl = s->desc.integrator == KHY_INT_VL2;
+        if (single_state(s)) KHY_CUDA(launch_dt_single(s->geom, s->U, s->clk, src, vl, s->stream));
+        else KHY_CUDA(s->desc.prec == KHY_PREC_FP64 ? launch_dt_fp64(s->geom, s->U, s->clk, src, vl, s->stream)
+                                                    : launch_dt_mixed(s->geom, s->U, s->clk, src, vl, s->stream));
+    }
+    if (s->desc.prec == KHY_PREC_FP64) {
+        KHY_CUDA(cudaMemcpyAsync(W, src, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        KHY_CUDA(cudaStreamSynchronize(s->stream));
+    } else {
+        std::vector<float> tmp(count);
+        KHY_CUDA(cudaMemcpyAsync(tmp.data(), src, count * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+        KHY_CUDA(cudaStreamSynchronize(s->stream));
+        for (size_t i = 0; i < count; ++i) W[i] = (double)tmp[i];
+    }
+    return KHY_OK;
+}
+
 khy_status khy_get_conserved_dev(khy_sim *s, double *U_dev, size_t count) {
     if (!s || !U_dev) return fail(KHY_ERR_ARG, "NULL argument");
     khy_status st = check_count(s, count);

@@ -37,6 +37,7 @@ EXPORTS = [
     "khy_set_conserved_dev", "khy_set_primitive_dev", "khy_set_time", "khy_step_to",
     "khy_enqueue_steps", "khy_get_conserved", "khy_get_conserved_dev", "khy_get_time", "khy_totals",
     "khy_get_flags", "khy_last_error", "khy_version", "khy_profile_steps", "khy_step_noalloc",
+    "khy_get_primitive",
     "khy_device_bytes",
     "khy_batch_create", "khy_batch_destroy", "khy_batch_set_primitive", "khy_batch_set_conserved",
     "khy_batch_get_conserved", "khy_batch_set_target", "khy_batch_enqueue_steps", "khy_batch_run",
@@ -112,6 +113,7 @@ def lib() -> ctypes.CDLL:
         "khy_enqueue_steps": [vp, d, l],
         "khy_get_conserved": [vp, vp, st],
         "khy_get_conserved_dev": [vp, vp, st],
+        "khy_get_primitive": [vp, vp, st],
         "khy_get_time": [vp, P(d), P(l), P(d)],
         "khy_totals": [vp, vp],
         "khy_get_flags": [vp, P(ctypes.c_uint), P(ctypes.c_ulonglong), i],
@@ -237,6 +239,11 @@ def khy_get_conserved(h, out) -> None:
         _check(lib().khy_get_conserved(h, p, out.size))
 
 
+def khy_get_primitive(h, out) -> None:
+    out, p = _host(out)
+    _check(lib().khy_get_primitive(h, p, out.size))
+
+
 def khy_profile_steps(h, t_end: float, nsteps: int) -> Tuple[float, float, float]:
     ms = (ctypes.c_float * 3)()
     _check(lib().khy_profile_steps(h, float(t_end), int(nsteps), ms))
@@ -330,6 +337,13 @@ class Sim:
         if out is None:
             out = np.empty(self.mesh.shape, dtype=np.float64)
         khy_get_conserved(self.h, out)
+        return out
+
+    def primitive(self, out=None):
+        """(rho, v.., p) as the library recovers them (flux precision, widened)."""
+        if out is None:
+            out = np.empty(self.mesh.shape, dtype=np.float64)
+        khy_get_primitive(self.h, out)
         return out
 
     def time(self) -> Tuple[float, int, float]:

@@ -306,6 +306,25 @@ def liska_wendroff(n: int = 400, size: float = 0.3, prec: int = PREC_FP64,
 # ---------------------------------------------------------- uniform state
 
 
+def cold_fast_state(ndim: int, n: Tuple[int, int, int], seed: int = 13,
+                    prec: int = PREC_MIXED) -> Tuple[Mesh, np.ndarray]:
+    """Fast, cold gas: rho in [0.5, 2], velocity components in [5, 10] with
+    random signs, pressure 1e-4 x [0.2, 2] (gamma 1.4): the kinetic energy is
+    ~2e5 times the internal energy; with a pressure floor of 1e-4 about half
+    of the cells are floored.  A stress state for the conserved-to-primitive
+    recovery (Sec. 3.1)."""
+    mesh = Mesh(ndim=ndim, n=tuple(n), gamma=1.4, cfl=0.4 if ndim < 3 else 0.3, prec=prec,
+                bc=_all_bc(BC_PERIODIC), p_floor=1e-4)
+    rng = np.random.default_rng(seed)
+    W = _empty(mesh)
+    sh = mesh.shape[1:]
+    W[0] = rng.uniform(0.5, 2.0, size=sh)
+    for d in range(ndim):
+        W[1 + d] = rng.uniform(5.0, 10.0, size=sh) * rng.choice([-1.0, 1.0], size=sh)
+    W[mesh.nvar - 1] = 1e-4 * rng.uniform(0.2, 2.0, size=sh)
+    return mesh, W
+
+
 def uniform(mesh: Mesh, rho: float = 1.0, v: Sequence[float] = (0.3, -0.2, 0.1), p: float = 0.7) -> np.ndarray:
     W = _empty(mesh)
     W[0] = rho
