@@ -172,6 +172,7 @@ template <class R>
 struct Consts {
     R gamma, gm1, g1, gp1, gm1_gp1;
     R igm1;  // 1 / (gamma - 1), FP32 path only
+    R hgp1;  // (gamma + 1) / 2, FP32 path only
 };
 
 template <class R>
@@ -180,9 +181,11 @@ __device__ __forceinline__ Consts<R> make_consts(const Geom &g) {
     if constexpr (sizeof(R) == 4) {
         c.gamma = g.f_gamma; c.gm1 = g.f_gm1; c.g1 = g.f_g1; c.gp1 = g.f_gp1; c.gm1_gp1 = g.f_gm1_gp1;
         c.igm1 = g.f_igm1;
+        c.hgp1 = 0.5f * g.f_gp1;  // exact
     } else {
         c.gamma = g.gamma; c.gm1 = g.gm1; c.g1 = g.g1; c.gp1 = g.gp1; c.gm1_gp1 = g.gm1_gp1;
         c.igm1 = 0.0;  // the FP64 flux divides by gamma - 1, as the reference does
+        c.hgp1 = 0.0;
     }
     return c;
 }

@@ -24,11 +24,6 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 div2(float2 a, float2 b) {
     return __fmul2_rn(a, make_float2(rcp_approx(b.x), rcp_approx(b.y)));
 }
-// sqrt(a), 0 for a <= 0: two reciprocal square roots, one packed multiply
-__device__ __forceinline__ float2 root2(float2 a) {
-    const float2 r = __fmul2_rn(a, make_float2(rsqrt_approx(a.x), rsqrt_approx(a.y)));
-    return make_float2(a.x > 0.f ? r.x : 0.f, a.y > 0.f ? r.y : 0.f);
-}
 // sqrt(a) for a >= 1
 __device__ __forceinline__ float2 root2_ge1(float2 a) {
     return __fmul2_rn(a, make_float2(rsqrt_approx(a.x), rsqrt_approx(a.y)));
@@ -63,16 +58,24 @@ __device__ __forceinline__ FF2 ff_add2(FF2 a, FF2 b) {
     return {hi, sub2(e, sub2(hi, s.hi))};
 }
 
-// minmod (Eq. 3): the smaller magnitude with the common sign, 0 if the signs
-// differ (or either is 0) -- the median of (0, a, b), four min/max operations.
-__device__ __forceinline__ float minmod1(float a, float b) {
-    return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.f));
+// a clamped to [lo, hi] per lane: with lo = min(b, 0), hi = max(b, 0) this is
+// minmod(a, b) of Eq. 3 (the value of the smaller magnitude when a and b share
+// a sign, otherwise 0; b when |a| = |b|) in two min/max operations per lane
+// once the bounds, which both sides of a face share, are formed
+__device__ __forceinline__ float2 clamp2(float2 a, float2 lo, float2 hi) {
+    return make_float2(fminf(fmaxf(a.x, lo.x), hi.x), fminf(fmaxf(a.y, lo.y), hi.y));
 }
-__device__ __forceinline__ float2 minmod2(float2 a, float2 b) { return make_float2(minmod1(a.x, b.x), minmod1(a.y, b.y)); }
 
 // HLLC flux of two faces (lanes), rotated primitives (rho, u, t_1..t_NT, p):
 // the same estimate of p* (PVRS, two-shock above both pressures), the same
-// Eq. 4 / Eq. 5 speeds and the same branch order as the scalar hllc().
+// Eq. 4 / Eq. 5 speeds and the same branch order as the scalar hllc(), with
+// the algebra arranged for few instructions: the star-state energy
+// rho*_K E*_K / rho*_K = rho_K Delta s_K / (s_K - s*) (E_K / rho_K + (s* - u_K)
+// (s* + p_K / (rho_K Delta s_K))) is formed as (Delta s_K E_K + (s* - u_K)
+// (m_K s* + p_K)) / (s_K - s*) with m_K = rho_K Delta s_K (no reciprocal of
+// rho_K or m_K), the transverse momentum fluxes are the mass flux times the
+// upwind transverse velocity, and the two-shock weights are reciprocal
+// square roots of (p* + B_K) / A_K.
 template <int NT>
 __device__ __forceinline__ void hllc2(const Consts<float> &k, const float2 (&wl)[NT + 3], const float2 (&wr)[NT + 3],
                                       float2 (&F)[NT + 3]) {
@@ -80,14 +83,13 @@ __device__ __forceinline__ void hllc2(const Consts<float> &k, const float2 (&wl)
     const float2 rl = wl[0], ul = wl[1], pl = wl[P];
     const float2 rr = wr[0], ur = wr[1], pr = wr[P];
     // c = sqrt(gamma p / rho) = a rsqrt(a rho) with a = gamma p: one
-    // special-function operation per lane; 0 where a = 0
+    // special-function operation per lane (a rho is clamped to the smallest
+    // normal float, so a = 0 gives c = 0)
     const float2 g = splat(k.gamma);
     const float2 al = mul2(g, pl), ar = mul2(g, pr);
-    const float2 xl = mul2(al, rl), xr = mul2(ar, rr);
-    float2 cl = mul2(al, make_float2(rsqrt_approx(xl.x), rsqrt_approx(xl.y)));
-    float2 cr = mul2(ar, make_float2(rsqrt_approx(xr.x), rsqrt_approx(xr.y)));
-    cl = make_float2(xl.x > 0.f ? cl.x : 0.f, xl.y > 0.f ? cl.y : 0.f);
-    cr = make_float2(xr.x > 0.f ? cr.x : 0.f, xr.y > 0.f ? cr.y : 0.f);
+    const float2 xl = max2(mul2(al, rl), splat(1.17549435e-38f)), xr = max2(mul2(ar, rr), splat(1.17549435e-38f));
+    const float2 cl = mul2(al, make_float2(rsqrt_approx(xl.x), rsqrt_approx(xl.y)));
+    const float2 cr = mul2(ar, make_float2(rsqrt_approx(xr.x), rsqrt_approx(xr.y)));
     const float2 du = sub2(ur, ul);
     // p_pvrs = (p_L + p_R)/2 - (u_R - u_L)(rho_L + rho_R)(c_L + c_R)/8
     const float2 ppv = mul2(splat(0.5f), fma2(mul2(du, add2(rl, rr)), mul2(splat(-0.25f), add2(cl, cr)), add2(pl, pr)));
@@ -95,9 +97,12 @@ __device__ __forceinline__ void hllc2(const Consts<float> &k, const float2 (&wl)
     const float2 pmax = max2(pl, pr);
     const bool tx = pstar.x > pmax.x, ty = pstar.y > pmax.y;
     if (tx || ty) {  // both waves shocks in at least one lane: two-shock estimate
-        const float2 two = splat(2.f), gp1 = splat(k.gp1), gg = splat(k.gm1_gp1);
-        const float2 gl = root2(div2(div2(two, mul2(gp1, rl)), fma2(gg, pl, pstar)));
-        const float2 gr = root2(div2(div2(two, mul2(gp1, rr)), fma2(gg, pr, pstar)));
+        // g_K = sqrt(A_K / (p* + B_K)), A_K = 2 / ((gamma + 1) rho_K), B_K = (gamma - 1)/(gamma + 1) p_K
+        const float2 hgp1 = splat(k.hgp1), gg = splat(k.gm1_gp1);
+        const float2 yl = mul2(fma2(gg, pl, pstar), mul2(hgp1, rl));
+        const float2 yr = mul2(fma2(gg, pr, pstar), mul2(hgp1, rr));
+        const float2 gl = make_float2(rsqrt_approx(yl.x), rsqrt_approx(yl.y));
+        const float2 gr = make_float2(rsqrt_approx(yr.x), rsqrt_approx(yr.y));
         const float2 pts = div2(sub2(fma2(gl, pl, mul2(gr, pr)), du), add2(gl, gr));
         pstar = sel2(tx, ty, pts, pstar);
     }
@@ -124,27 +129,28 @@ __device__ __forceinline__ void hllc2(const Consts<float> &k, const float2 (&wl)
     const float2 rk = w[0], uk = w[1], pk = w[P];
     const float2 sk = sel2(lx, ly, sl, sr);
     const float2 mk = sel2(lx, ly, ml, mr);
+    const float2 dsk = sel2(lx, ly, dsl, dsr);
     float2 vsq = mul2(uk, uk);
 #pragma unroll
     for (int j = 0; j < NT; ++j) vsq = fma2(w[2 + j], w[2 + j], vsq);
     const float2 E = fma2(mul2(splat(0.5f), rk), vsq, mul2(pk, splat(k.igm1)));
     const float2 mf = mul2(rk, uk);
-    // F_K, and F = F_K + s_K (U*_K - U_K) with s_K and the star factor
-    // rho_K Delta s_K / (s_K - s*) zeroed where F_K itself is the flux
-    // (supersonic lanes: the correction vanishes exactly and stays finite)
+    // F_K, and F = F_K + s_K (U*_K - U_K) with s_K and r = 1 / (s_K - s*)
+    // zeroed where F_K itself is the flux (supersonic lanes: the correction
+    // vanishes exactly and stays finite)
     const float2 zero = splat(0.f);
     const float2 skm = sel2(ox, oy, zero, sk);
-    const float2 fac = sel2(ox, oy, zero, div2(mk, sub2(sk, sstar)));
-    const float2 d0 = sub2(fac, rk);  // rho*_K - rho_K; transverse: (rho*_K - rho_K) t
-    const float2 sd0 = mul2(skm, d0);
+    const float2 dss = sub2(sk, sstar);
+    const float2 r = sel2(ox, oy, zero, make_float2(rcp_approx(dss.x), rcp_approx(dss.y)));
+    const float2 fac = mul2(mk, r);  // rho*_K
+    const float2 sd0 = mul2(skm, sub2(fac, rk));
     F[0] = add2(mf, sd0);
     F[1] = fma2(skm, sub2(mul2(fac, sstar), mf), fma2(mf, uk, pk));
 #pragma unroll
-    for (int j = 0; j < NT; ++j) F[2 + j] = fma2(sd0, w[2 + j], mul2(mf, w[2 + j]));
-    // E*_K / rho*_K = E_K / rho_K + (s* - u_K)(s* + p_K / m_K)
-    const float2 X = fma2(sub2(sstar, uk), fma2(pk, make_float2(rcp_approx(mk.x), rcp_approx(mk.y)), sstar),
-                          mul2(E, make_float2(rcp_approx(rk.x), rcp_approx(rk.y))));
-    F[P] = fma2(skm, sub2(mul2(fac, X), E), mul2(add2(E, pk), uk));
+    for (int j = 0; j < NT; ++j) F[2 + j] = mul2(F[0], w[2 + j]);
+    // rho*_K E*_K / rho*_K as (Delta s_K E_K + (s* - u_K)(m_K s* + p_K)) r
+    const float2 facX = mul2(r, fma2(sub2(sstar, uk), fma2(mk, sstar, pk), mul2(dsk, E)));
+    F[P] = fma2(skm, sub2(facX, E), mul2(add2(E, pk), uk));
 }
 
 // Storage slot of rotated component j (0 rho, 1 normal velocity, 2..ND
@@ -175,9 +181,14 @@ __device__ __forceinline__ void face_flux2(const float2 (&st)[4][ND + 2], const 
             wr[j] = st[2][j];
             continue;
         }
+        // minmod (Eq. 3) of the difference across the face with the one on
+        // either side, as clamps to the interval between 0 and the face
+        // difference (the bounds are shared by both sides)
         const float2 d12 = sub2(st[2][j], st[1][j]);
-        wl[j] = fma2(minmod2(sub2(st[1][j], st[0][j]), d12), half, st[1][j]);
-        wr[j] = fma2(minmod2(d12, sub2(st[3][j], st[2][j])), mhalf, st[2][j]);
+        const float2 lo = make_float2(fminf(d12.x, 0.f), fminf(d12.y, 0.f));
+        const float2 hi = make_float2(fmaxf(d12.x, 0.f), fmaxf(d12.y, 0.f));
+        wl[j] = fma2(clamp2(sub2(st[1][j], st[0][j]), lo, hi), half, st[1][j]);
+        wr[j] = fma2(clamp2(sub2(st[3][j], st[2][j]), lo, hi), mhalf, st[2][j]);
     }
     hllc2<NT>(k, wl, wr, Fr);
 }
