@@ -63,6 +63,8 @@
 
 namespace khy {
 
+constexpr int kMaxChunks = 96;  // runs of planes per tile column (stage_kernel work split)
+
 struct StageArgs {
     Geom g;
     const double *Uin;    // state the stage adds to: Un (1, 3, 5) or U1 (2, 6); unused in 4
@@ -72,6 +74,11 @@ struct StageArgs {
     void *Wout;           // primitives written (3: W^{n+1/2}, 5: W^1, 6: W^{n+1})
     Clock *clk;
     int cubic;            // mixed path: all active dx equal (one dt/dx factor)
+    int nchunk;           // work split (stage_kernel): 0 = one contiguous share of the
+                          // (tile, plane) sequence per CTA; > 0 = each tile column cut
+                          // into nchunk runs of planes [kb[c], kb[c + 1]), one run per
+                          // CTA, chunk-major
+    int kb[kMaxChunks + 1];
 };
 
 template <int ND, int TX, int TY>
@@ -837,11 +844,34 @@ __global__ void __launch_bounds__(cta_threads<R, ND, TX, TY>(), MinBlocks<R, cta
     const int nty = (ND == 3) ? (g.n[1] + TY - 1) / TY : 1;
     const int nm = (ND >= 2) ? g.n[DM] : 1;
     const long long total = (long long)ntx * nty * nm;
-    const long long s0 = total * blockIdx.x / gridDim.x;
-    const long long s1 = total * (blockIdx.x + 1) / gridDim.x;
 
     unsigned flags = 0, floors = 0;
     double wmin = __longlong_as_double((long long)kInfBits);
+    if (a.nchunk > 0 && ND >= 2) {
+        // unit = one run of planes [kb[c], kb[c + 1]) of one tile column,
+        // numbered chunk-major: CTAs that run at the same
+        // time hold neighbouring tiles at the same planes, so the halo rows
+        // they share are read from HBM once and from L2 after that, and the
+        // hardware hands the units to CTA slots as they free up
+        const long long ntile = (long long)ntx * nty;
+        const int nch = a.nchunk;
+        const long long units = ntile * nch;
+        for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+            const long long tile = u % ntile;
+            const int c = (int)(u / ntile);
+            const int k0 = a.kb[c], k1 = a.kb[c + 1];
+            const int x0 = (int)(tile % ntx) * TX;
+            const int y0 = (ND == 3) ? (int)(tile / ntx) * TY : 0;
+            run_segment<R, ND, STAGE, TX, TY, S>(g, reinterpret_cast<const S *>(a.Uin), reinterpret_cast<const S *>(a.Ubase),
+                                                 reinterpret_cast<S *>(a.Uout), reinterpret_cast<const R *>(a.Win),
+                                                 reinterpret_cast<R *>(a.Wout), dtdx, a.cubic, x0, y0, k0, k1, sW, sFx,
+                                                 sFy, flags, floors, wmin);
+        }
+        reduce_to_clock<STAGE, NTH>(a.clk, flags, floors, wmin);
+        return;
+    }
+    const long long s0 = total * blockIdx.x / gridDim.x;
+    const long long s1 = total * (blockIdx.x + 1) / gridDim.x;
     for (long long pos = s0; pos < s1;) {
         const long long tile = pos / nm;
         const int k0 = (int)(pos % nm);
