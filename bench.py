@@ -46,10 +46,10 @@ STAGE_SOURCES = ("khy_mixed.cu", "khy_launch.cuh", "khy_internal.h", "khy_stage.
                  "khy_mixed_kernels.cuh", "khy_packed.cuh", "khy_single_kernels.cuh")
 
 
-def stage_sources_sha256() -> str:
+def stage_sources_sha256(sources=STAGE_SOURCES) -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in STAGE_SOURCES:
+    for name in sources:
         with open(os.path.join(ROOT, "paper_2501_02317_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -69,6 +69,14 @@ def _recorded_traffic(workload: str):
         return None
 
 
+def _sm_max_mhz() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -76,6 +84,57 @@ def _peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def host_cpu() -> dict:
+    """Host CPU model and logical CPU count (lscpu / nproc)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
+# the translation unit of the all-FP64 stage kernels and every file it includes
+FP64_SOURCES = ("khy_fp64.cu", "khy_launch.cuh", "khy_internal.h", "khy_stage.cuh", "khy_kernels.cuh",
+                "khy_mixed_kernels.cuh", "khy_packed.cuh", "khy_single_kernels.cuh")
+# FP64 instructions a GB300 SM retires per clock (DFMA, DADD, DMUL: two
+# lanes per clock per SM, the rate behind the part's nominal 1.25 TFLOP/s
+# of FP64 FMA at 152 SMs and 2.07 GHz)
+FP64_PER_CLK_PER_SM = 2
+
+
+def fp64_ops_per_cell_update(workload: str):
+    """Thread-level FP64 instructions (DFMA + DADD + DMUL) per cell-update of
+    the all-FP64 stage pair, from the committed ncu count, or None when the
+    FP64 kernels' sources changed since it was taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "fp64_stage_ops.json")) as f:
+            rec = json.load(f)
+        if rec.get("sources_sha256") != stage_sources_sha256(FP64_SOURCES) or rec.get("workload") != workload:
+            return None
+        return float(rec["fp64_inst_per_cell_update"])
+    except Exception:
+        return None
+
+
+def fp64_roofline(stage_ms: float, ncell: int, workload: str, sms: int, sm_mhz: float):
+    """Bound of the all-FP64 leg: counted FP64 instructions per cell-update x
+    cells over the stage pair's event-timed duration, against the FP64 pipe's
+    peak (FP64_PER_CLK_PER_SM x SMs x the maximum SM clock)."""
+    ops = fp64_ops_per_cell_update(workload)
+    peak = FP64_PER_CLK_PER_SM * sms * sm_mhz * 1e6
+    if ops is None:
+        return {"bound": "fp64", "achieved": None, "peak": peak / 1e12, "unit": "T FP64 inst/s", "frac": None,
+                "ops_per_cell_update": None, "note": "no FP64 instruction count recorded for these sources"}
+    ach = ops * ncell / (stage_ms * 1e-3)
+    return {"bound": "fp64", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "T FP64 inst/s",
+            "frac": ach / peak, "ops_per_cell_update": ops, "peak_kind": "nominal (2 per clock per SM)"}
 
 
 class ClockSampler:
@@ -136,23 +195,53 @@ class ClockSampler:
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
 
-def cpu_oracle_rate(seconds: float = 10.0, n: int = 128, threads: int = 0):
-    """Oracle cell-updates/s on an n^3 turbulence box with `threads` host
-    threads (0: all cores); at least one step."""
+def cpu_oracle_rate(steps: int = 10, n: int = 256, threads: int = 0):
+    """Oracle cell-updates/s over `steps` Heun steps of the n^3 turbulence
+    box (the headline workload) with `threads` host threads (0: all cores).
+    Returns (rate, threads used, sample description, final state, mesh, W)."""
     import oracle
     from paper_2501_02317_gb300 import workloads as wl
     cores = threads or os.cpu_count() or 1
     used = oracle.set_threads(cores)
     mesh, W = wl.turbulence(n, prec=wl.PREC_FP64)
     U = oracle.prim_to_cons(mesh, W)
-    t, steps, t0 = 0.0, 0, time.perf_counter()
-    while True:
+    t = 0.0
+    t0 = time.perf_counter()
+    for _ in range(steps):
         U, t, _, _ = oracle.heun_step(mesh, U, t, 1e30)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    return mesh.ncell * steps / el, used, "%d Heun steps of the %d^3 turbulence box (same recipe, seed 2)" % (steps, n)
+    el = time.perf_counter() - t0
+    sample = "%d Heun step%s of the %d^3 turbulence box (the headline workload, seed 2)" % (
+        steps, "" if steps == 1 else "s", n)
+    return mesh.ncell * steps / el, used, sample, U, mesh, W
+
+
+def parity_against_oracle(khydro, wl, mesh0, W, Uo, steps: int):
+    """Per-field relative L1 (sum |q - q_ref| / sum |q_ref|, conserved fields
+    and the pressure) of the mixed and all-FP64 paths after `steps` Heun steps
+    of the headline workload against the oracle's state after the same steps
+    (the state the CPU-baseline leg computed)."""
+    out = {}
+    for name, prec in (("mixed", wl.PREC_MIXED), ("fp64", wl.PREC_FP64)):
+        mesh = mesh0.replace(prec=prec)
+        with khydro.Sim(mesh) as sim:
+            sim.set_primitive(W)
+            sim.step_to(1e30, steps)
+            U = sim.conserved()
+        errs = {}
+        names = ["rho"] + ["m_%s" % "xyz"[d] for d in range(mesh.ndim)] + ["E"]
+        for q, nm in enumerate(names):
+            errs[nm] = float(np.abs(U[q] - Uo[q]).sum() / np.abs(Uo[q]).sum())
+
+        def pres(V):
+            ke = 0.5 * sum(V[1 + d] ** 2 for d in range(mesh.ndim)) / V[0]
+            return (mesh.gamma - 1.0) * (V[mesh.nvar - 1] - ke)
+        po = pres(Uo)
+        errs["p"] = float(np.abs(pres(U) - po).sum() / np.abs(po).sum())
+        errs["bitwise"] = bool(np.array_equal(U, Uo))
+        out[name] = errs
+    out["steps"] = steps
+    out["gates"] = {"fp64": "1e-12 every field", "mixed": "rho 1e-5, p 1e-4"}
+    return out
 
 
 def bench_batch(khydro, wl, torch, steps: int = 200):
@@ -184,15 +273,17 @@ def bench_batch(khydro, wl, torch, steps: int = 200):
             "variant": variant, "ctas": info["nblocks"], "launches_per_step": 3, "all_grids_stepped": done}
 
 
-def bench_serving(khydro, wl, njobs: int = 60, budget_bytes: int = 16 << 30, slots: int = 64):
-    """Serving: the first `njobs` jobs of the seeded Poisson stream (200/s;
-    2D 64^2-512^2 and 3D 32^3-128^3, KH / blast / turbulence, t_end U[0.05, 0.5])
-    submitted at their arrival times; then the same jobs at 50% and 90% of the
-    measured capacity.  Time-to-solution = finish - submit."""
+def bench_serving(khydro, wl, njobs: int = 1000, budget_bytes: int = 16 << 30, slots: int = 64):
+    """Serving: the first `njobs` jobs of the seeded Poisson stream (mean 200
+    jobs/s; 2D 64^2-512^2 and 3D 32^3-128^3, KH / blast / turbulence, t_end
+    U[0.05, 0.5]) submitted at their arrival times; then the same jobs as
+    Poisson streams at 50% and 90% of the capacity measured in the first run
+    (the stream's exponential inter-arrival times rescaled to the lower rate).
+    Time-to-solution = finish - submit."""
     jobs = wl.serving_stream(njobs, seed=4)
     ics = [wl.job_initial_state(j) for j in jobs]
 
-    def run(arrivals):
+    def run(arrivals, offered):
         with khydro.Server(budget_bytes, slots) as srv:
             t0 = time.perf_counter()
             ids = []
@@ -209,20 +300,22 @@ def bench_serving(khydro, wl, njobs: int = 60, budget_bytes: int = 16 << 30, slo
                 lat.append(td - ts)
             st = srv.stats()
         makespan = st["elapsed_s"]
-        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+        return {"arrivals": "poisson", "offered_jobs_per_s": offered, "achieved_jobs_per_s": len(ids) / makespan,
+                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                 "value": st["cell_updates"] / makespan, "jobs": len(ids), "makespan_s": makespan,
                 "cell_updates": st["cell_updates"]}
 
     base = [j.arrival for j in jobs]
-    sat = run(base)
-    cap = njobs / sat["makespan_s"]  # jobs/s the server sustained while saturated
+    rate0 = 200.0
+    sat = run(base, rate0)
+    cap = sat["achieved_jobs_per_s"]  # jobs/s the server sustained while saturated
     out = {"workload": "Poisson 200 jobs/s (seed 4), first %d jobs, mixed, HBM budget %d GiB, %d slots"
                        % (njobs, budget_bytes >> 30, slots),
            "offered_200_per_s": sat, "capacity_jobs_per_s": cap}
     for frac in (0.5, 0.9):
         rate = frac * cap
-        arr = [k / rate for k in range(njobs)]
-        out["load_%d%%" % int(frac * 100)] = run(arr)
+        arr = [a * rate0 / rate for a in base]  # the same exponential gaps, mean 1/rate
+        out["load_%d%%" % int(frac * 100)] = run(arr, rate)
     out["unit"] = UNIT
     return out
 
@@ -266,7 +359,7 @@ def run_reference(args):
     from paper_2501_02317_gb300 import workloads as wl
     cores = os.cpu_count() or 1
     used = oracle.set_threads(cores)
-    n = 128
+    n = args.n
     mesh, W = wl.turbulence(n, prec=wl.PREC_FP64)
     U = oracle.prim_to_cons(mesh, W)
     t = 0.0
@@ -277,13 +370,13 @@ def run_reference(args):
         U, t, _, _ = oracle.heun_step(mesh, U, t, 1e30)
     el = time.perf_counter() - t0
     value = mesh.ncell * args.steps / el
-    sample = "one oracle Heun step of a %d^3 turbulence box (same recipe as the 256^3 workload) per step" % n
+    sample = "one oracle Heun step of the whole %d^3 turbulence box (the headline workload) per step" % n
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "turbulence-3d-%d^3-mixed" % args.n, "cells": (args.n ** 3),
-                   "sample": "oracle (FP64) on a %d^3 box of the same recipe, %d cells" % (n, mesh.ncell)},
+        "config": {"workload": "turbulence-3d-%d^3-mixed" % n, "cells": mesh.ncell,
+                   "sample": "oracle (FP64) on the same %d^3 box, %d cells, %d threads" % (n, mesh.ncell, used)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -302,6 +395,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-grids measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the FP64, FP32, van Leer and lean-Heun legs (headline only)")
+    ap.add_argument("--serve-jobs", type=int, default=1000, help="jobs of the serving stream")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -359,16 +455,24 @@ def main():
     achieved = BYTES_PER_CELL_UPDATE_3D * ncell / (stage_ms * 1e-3) / 1e9
 
     # ---------------------------------------------------------- all-FP64 path
-    mesh64 = mesh.replace(prec=wl.PREC_FP64)
-    sim64 = khydro.Sim(mesh64, stream=stream.cuda_stream)
-    sim64.set_primitive(W)
-    sim64.enqueue_steps(T_END, 2)
-    torch.cuda.synchronize()
-    k64 = max(3, K // 10)
-    el64 = max_over_ranks(timed_steps(sim64, k64))
-    value64 = whole_job_rate(world, ncell * k64, el64)
-    ms64 = sim64.profile_steps(T_END, 2)
-    sim64.close()
+    fp64 = None
+    value64 = None
+    if not args.no_legs:
+        mesh64 = mesh.replace(prec=wl.PREC_FP64)
+        sim64 = khydro.Sim(mesh64, stream=stream.cuda_stream)
+        sim64.set_primitive(W)
+        sim64.enqueue_steps(T_END, 2)
+        torch.cuda.synchronize()
+        k64 = max(3, K // 10)
+        el64 = max_over_ranks(timed_steps(sim64, k64))
+        value64 = whole_job_rate(world, ncell * k64, el64)
+        ms64 = sim64.profile_steps(T_END, 2)
+        sim64.close()
+        fp64 = {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": 1e3 * el64 / k64,
+                "stage_ms": [ms64[1], ms64[2]],
+                "roofline": fp64_roofline(ms64[1] + ms64[2], ncell, "turbulence-3d-fp64",
+                                          torch.cuda.get_device_properties(local).multi_processor_count,
+                                          _sm_max_mhz())}
 
     # ---------------------------------------------------------- all-FP32 path, van Leer (mixed)
     def leg(prec, integrator, k, bytes_per_cu):
@@ -386,9 +490,14 @@ def main():
                 "stage_ms": [pm[1], pm[2]], "state_bytes": state_bytes, "bytes_per_cell_update": bytes_per_cu,
                 "hbm_achieved_gbs": ach, "hbm_frac": ach / peak_gbs}
 
-    fp32 = leg(wl.PREC_FP32, wl.INT_HEUN, K, BYTES_PER_CELL_UPDATE_3D_FP32)
-    vl2 = leg(wl.PREC_MIXED, wl.INT_VL2, K, BYTES_PER_CELL_UPDATE_3D_VL2)
-    lean = leg(wl.PREC_MIXED, wl.INT_HEUN_LEAN, K, BYTES_PER_CELL_UPDATE_3D)
+    fp32 = vl2 = lean = None
+    if not args.no_legs:
+        fp32 = dict(leg(wl.PREC_FP32, wl.INT_HEUN, K, BYTES_PER_CELL_UPDATE_3D_FP32),
+                    workload="turbulence-3d-%d^3-fp32 (FP32 state and flux)" % args.n)
+        vl2 = dict(leg(wl.PREC_MIXED, wl.INT_VL2, K, BYTES_PER_CELL_UPDATE_3D_VL2),
+                   workload="turbulence-3d-%d^3-mixed, memory-optimized van Leer integrator" % args.n)
+        lean = dict(leg(wl.PREC_MIXED, wl.INT_HEUN_LEAN, K, BYTES_PER_CELL_UPDATE_3D),
+                    workload="turbulence-3d-%d^3-mixed, Heun without stored primitives" % args.n)
 
     # ---------------------------------------------------------- end to end (host buffers)
     e2e = None
@@ -411,15 +520,21 @@ def main():
     sim.close()
 
     batch = None if args.no_batch or world > 1 else bench_batch(khydro, wl, torch)
-    serving = None if args.no_serve or world > 1 else bench_serving(khydro, wl)
+    serving = None if args.no_serve or world > 1 else bench_serving(khydro, wl, njobs=args.serve_jobs)
 
     cpu = None
+    parity = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, cores, sample = cpu_oracle_rate()
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        csteps = 10
+        v, cores, sample, Uo, _, W0 = cpu_oracle_rate(steps=csteps, n=args.n)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "host": host_cpu()}
         # the plain single-thread oracle beside the OpenMP build (same bits)
-        v1, _, sample1 = cpu_oracle_rate(seconds=5.0, threads=1)
+        v1, _, sample1, _, _, _ = cpu_oracle_rate(steps=1, n=args.n, threads=1)
         cpu["single_thread"] = {"value": v1, "unit": UNIT, "cores": 1, "sample": sample1}
+        # the oracle's state after those steps is the reference of the
+        # per-field errors of both GPU paths over the same steps
+        parity = parity_against_oracle(khydro, wl, mesh, W0, Uo, csteps)
 
     if rank == 0:
         line = {
@@ -429,12 +544,12 @@ def main():
             "config": {"workload": "turbulence-3d-%d^3-mixed" % args.n, "cells": ncell, "prec": "mixed",
                        "cfl": mesh.cfl, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2: two 5x8xN-byte states (%.0f MB each)" % (mesh.nvar * 8 * ncell / 1e6)},
-            "fp64": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": 1e3 * el64 / k64,
-                     "stage_ms": [ms64[1], ms64[2]]},
-            "mixed_over_fp64": value / value64,
-            "fp32": dict(fp32, workload="turbulence-3d-%d^3-fp32 (FP32 state and flux)" % args.n),
-            "vl2_mixed": dict(vl2, workload="turbulence-3d-%d^3-mixed, memory-optimized van Leer integrator" % args.n),
-            "heun_lean_mixed": dict(lean, workload="turbulence-3d-%d^3-mixed, Heun without stored primitives" % args.n),
+            "fp64": fp64,
+            "mixed_over_fp64": value / value64 if value64 else None,
+            "fp32": fp32,
+            "vl2_mixed": vl2,
+            "heun_lean_mixed": lean,
+            "parity_256": parity,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                          "frac": achieved / peak_gbs,
                          "traffic": _recorded_traffic("turbulence-3d-%d^3-mixed" % args.n),
