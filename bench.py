@@ -255,6 +255,7 @@ def bench_batch(khydro, wl, torch, steps: int = 200):
     with khydro.Batch(meshes, stream=stream.cuda_stream) as b:
         b.set_primitive([W for _, W in grids])
         variant, tune_ms = b.autotune(2)
+        _, ctas_per_slot = b.schedule()
         b.set_target(1e30, steps)
         b.enqueue_steps(3)
         torch.cuda.synchronize()
@@ -270,7 +271,7 @@ def bench_batch(khydro, wl, torch, steps: int = 200):
         done = all(b.clock(k)[1] == steps + 3 for k in (0, len(meshes) // 2, len(meshes) - 1))
     return {"workload": "4096 2D blast grids, sides log-U[32,256] (seed 3), mixed, periodic", "grids": len(meshes),
             "cells": cells, "steps": steps, "value": cells * steps / el, "unit": UNIT, "ms_per_step": 1e3 * el / steps,
-            "variant": variant, "ctas": info["nblocks"], "launches_per_step": 3, "all_grids_stepped": done}
+            "variant": variant, "ctas_per_slot": ctas_per_slot, "ctas": info["nblocks"], "launches_per_step": 3, "all_grids_stepped": done}
 
 
 def bench_serving(khydro, wl, njobs: int = 1000, budget_bytes: int = 16 << 30, slots: int = 64):

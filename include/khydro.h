@@ -237,15 +237,28 @@ khy_status khy_batch_run(khy_batch *b, long *batch_steps);
 /* Time, steps taken and last dt of one grid.  Synchronises. */
 khy_status khy_batch_get_clock(khy_batch *b, int grid, double *t, long *steps, double *dt);
 
-/* Autotuner: times every tile variant of the batch's dimensionality for
- * trial_steps steps on the current state (state and clocks are restored
- * afterwards), keeps the fastest and remembers it for batches of the same
- * shape (ndim, prec, grid count, cell count).  Synchronises. */
+/* Autotuner: times every schedule -- tile variant x CTAs per resident CTA
+ * slot in {1, 4, 16, 32} -- for trial_steps steps on the current state
+ * (state and clocks are restored afterwards), keeps the fastest and
+ * remembers it for batches of the same shape class (ndim, prec, grid count
+ * and cell-weighted mean grid side, each to a power of two); new batches of
+ * that class start with it.  *variant receives the tile variant (the CTAs
+ * per slot: khy_batch_get_schedule).  Synchronises. */
 khy_status khy_batch_autotune(khy_batch *b, int trial_steps, int *variant, float *ms_per_step);
 
-/* Selects a tile variant explicitly: 1D 0..1 (rows of 128, 256), 2D 0..4
- * (rows of 64, 128, 256, 124, 252), 3D 0..2 (32x8, 32x16, 64x8); see
- * khy_batch_info.  Other values: KHY_ERR_ARG. */
+/* Selects a schedule explicitly: tile variant (as khy_batch_set_variant)
+ * and ctas_per_slot in [1, 256], the number of equal-cost pieces the tile
+ * runs are cut into per resident CTA slot (default 16: more pieces than
+ * slots, which the hardware balances).  Results do not depend on the
+ * schedule.  Errors: KHY_ERR_ARG. */
+khy_status khy_batch_set_schedule(khy_batch *b, int variant, int ctas_per_slot);
+
+/* Current tile variant and CTAs per resident slot (either may be NULL). */
+khy_status khy_batch_get_schedule(khy_batch *b, int *variant, int *ctas_per_slot);
+
+/* Selects a tile variant explicitly (keeping the CTAs per slot): 1D 0..1
+ * (rows of 128, 256), 2D 0..4 (rows of 64, 128, 256, 124, 252), 3D 0..2
+ * (32x8, 32x16, 64x8); see khy_batch_info.  Other values: KHY_ERR_ARG. */
 khy_status khy_batch_set_variant(khy_batch *b, int variant);
 
 /* Like khy_profile_steps for a batch: average ms of the clock, stage-1 and

@@ -9,13 +9,16 @@
 // at the same offsets (the stage kernels read them instead of recovering halo
 // cells, as a single grid's Heun step does); every grid has its own clock,
 // so its own dt (Sec. 3.1) and its own target time.  One Heun step of the whole batch is three launches: a clock
-// launch (one thread per grid), and one persistent launch per stage that
-// covers every grid through a precomputed segment schedule (tile runs of
-// planes, balanced by cells over the resident CTAs).  K steps are recorded
+// launch (one thread per grid), and one launch per stage that covers every
+// grid through a precomputed segment schedule (tile runs of planes, cut into
+// pieces of equal estimated cost, several per resident CTA slot).  K steps are recorded
 // once in a CUDA graph and replayed.
 //
-// The tile shape is a "variant"; khy_batch_autotune times every variant on
-// the batch's own state and keeps the fastest (cached per batch shape).
+// The tile shape is a "variant" and the schedule cuts the work into
+// ctas_per_slot pieces per resident CTA slot; khy_batch_autotune times every
+// (variant, ctas_per_slot) pair on the batch's own state and keeps the
+// fastest, cached per shape class (dimensionality, precision, grid count and
+// mean grid side, each to a power of two).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -115,8 +118,20 @@ Schedule build_schedule(const std::vector<GridDesc> &gd, int ndim, int TX, int T
     return s;
 }
 
+// The schedule of a batch cuts its tile runs into ctas_per_slot x (resident
+// CTA slots) pieces of equal estimated cost: more pieces than slots, so the
+// hardware hands pieces to slots as they free up and no CTA waits for a
+// slower one (the cost model ignores the small grids' fixed overheads).
+// 4096-grid 2D batch, mixed, tile rows of 124, cell-updates/s: 1 -> 1.24e10,
+// 4 -> 1.32e10, 8 -> 1.38e10, 16 -> 1.44e10, 32 -> 1.45e10, 64 -> 1.33e10.
+constexpr int kDefaultCtasPerSlot = 16;
+constexpr int kTunedCtasPerSlot[] = {1, 4, 16, 32};
+
+// Tuned (variant, ctas per slot) per batch shape class: dimensionality,
+// precision, log2 of the grid count and log2 of the cell-weighted mean grid
+// side (so batches of similar grid sizes share a tuning).
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, long long>, int> g_tune_cache;  // (ndim, prec, ngrids, cells) -> variant
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
 
 }  // namespace
 
@@ -140,6 +155,7 @@ struct khy_batch {
     int *d_cta = nullptr;
     int nblocks = 0;
     int variant = -1;
+    int ctas_per_slot = kDefaultCtasPerSlot;
     cudaGraphExec_t graph = nullptr;
     bool wmin_valid = false;
 };
@@ -178,13 +194,23 @@ MultiArgs args_of(const khy_batch *b, int stage) {
     return a;
 }
 
-khy_status apply_variant(khy_batch *b, int v) {
+// Class of a batch for the tuning cache.
+std::tuple<int, int, int, int> shape_class(const khy_batch *b) {
+    double side = 0.0;  // cell-weighted mean side
+    for (const GridDesc &g : b->gd) side += (double)g.g.ncell * std::pow((double)g.g.ncell, 1.0 / b->ndim);
+    side /= (double)std::max<long long>(1, b->cells);
+    return std::make_tuple(b->ndim, b->prec, (int)std::floor(std::log2((double)b->ngrids)),
+                           (int)std::floor(std::log2(std::max(1.0, side))));
+}
+
+khy_status apply_schedule(khy_batch *b, int v, int ctas_per_slot) {
     int tx = 0, ty = 0;
     multi_variant_tile(b->ndim, v, &tx, &ty);
     if (tx == 0) return bfail(KHY_ERR_ARG, "khy_batch: no such tile variant");
+    if (ctas_per_slot < 1 || ctas_per_slot > 256) return bfail(KHY_ERR_ARG, "khy_batch: ctas_per_slot must be in [1, 256]");
     const int resident = multi_resident(b->prec == KHY_PREC_FP64, b->ndim, v);
     if (resident <= 0) return bfail(KHY_ERR_CUDA, "khy_batch: kernel occupancy query failed");
-    Schedule s = build_schedule(b->gd, b->ndim, tx, ty, resident);
+    Schedule s = build_schedule(b->gd, b->ndim, tx, ty, ctas_per_slot * resident);
     cudaFree(b->d_segs);
     cudaFree(b->d_cta);
     b->d_segs = nullptr;
@@ -198,6 +224,7 @@ khy_status apply_variant(khy_batch *b, int v) {
     KHY_BCUDA(cudaStreamSynchronize(b->stream));
     b->nblocks = s.nblocks;
     b->variant = v;
+    b->ctas_per_slot = ctas_per_slot;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -436,13 +463,16 @@ khy_status khy_batch_create(const khy_mesh_desc *descs, int ngrids, void *cuda_s
         khy_batch_destroy(b);
         return bfail(e == cudaErrorMemoryAllocation ? KHY_ERR_OOM : KHY_ERR_CUDA, cudaGetErrorString(e));
     }
-    int v = 0;
-    {  // a previously tuned variant for the same batch shape, else variant 0
+    int v = 0, cps = kDefaultCtasPerSlot;
+    {  // a schedule tuned for the same shape class, else variant 0
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(std::make_tuple(b->ndim, b->prec, ngrids, b->cells));
-        if (it != g_tune_cache.end()) v = it->second;
+        auto it = g_tune_cache.find(shape_class(b));
+        if (it != g_tune_cache.end()) {
+            v = it->second.first;
+            cps = it->second.second;
+        }
     }
-    khy_status st = apply_variant(b, v);
+    khy_status st = apply_schedule(b, v, cps);
     if (st != KHY_OK) {
         khy_batch_destroy(b);
         return st;
@@ -558,7 +588,19 @@ khy_status khy_batch_get_clock(khy_batch *b, int grid, double *t, long *steps, d
 
 khy_status khy_batch_set_variant(khy_batch *b, int variant) {
     if (!b) return bfail(KHY_ERR_ARG, "khy_batch_set_variant: NULL batch");
-    return apply_variant(b, variant);
+    return apply_schedule(b, variant, b->ctas_per_slot);
+}
+
+khy_status khy_batch_set_schedule(khy_batch *b, int variant, int ctas_per_slot) {
+    if (!b) return bfail(KHY_ERR_ARG, "khy_batch_set_schedule: NULL batch");
+    return apply_schedule(b, variant, ctas_per_slot);
+}
+
+khy_status khy_batch_get_schedule(khy_batch *b, int *variant, int *ctas_per_slot) {
+    if (!b) return bfail(KHY_ERR_ARG, "khy_batch_get_schedule: NULL batch");
+    if (variant) *variant = b->variant;
+    if (ctas_per_slot) *ctas_per_slot = b->ctas_per_slot;
+    return KHY_OK;
 }
 
 khy_status khy_batch_profile_steps(khy_batch *b, long nsteps, float ms[3]) {
@@ -609,18 +651,19 @@ khy_status khy_batch_autotune(khy_batch *b, int trial_steps, int *variant, float
     e = cudaMemcpyAsync(saved, b->U, sizeof(double) * b->pool, cudaMemcpyDeviceToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(saved_clk, b->d_clocks, sizeof(Clock) * b->ngrids, cudaMemcpyDeviceToDevice, b->stream);
-    const int v0 = b->variant;
-    int best = v0;
+    int best = b->variant, best_cps = b->ctas_per_slot;
     float best_ms = 1e30f;
     khy_status st = KHY_OK;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    for (int v = 0; v < kMultiVariants && e == cudaSuccess && st == KHY_OK; ++v) {
+    constexpr int ncps = (int)(sizeof(kTunedCtasPerSlot) / sizeof(kTunedCtasPerSlot[0]));
+    for (int trial = 0; trial < kMultiVariants * ncps && e == cudaSuccess && st == KHY_OK; ++trial) {
+        const int v = trial / ncps, cps = kTunedCtasPerSlot[trial % ncps];
         int tx = 0, ty = 0;
         multi_variant_tile(b->ndim, v, &tx, &ty);
         if (tx == 0) continue;
-        if ((st = apply_variant(b, v)) != KHY_OK) break;
+        if ((st = apply_schedule(b, v, cps)) != KHY_OK) break;
         multi_target_kernel<<<(b->ngrids + 127) / 128, 128, 0, b->stream>>>(b->d_clocks, 0, b->ngrids, INFINITY,
                                                                              (long long)trial_steps + 1);
         b->wmin_valid = false;
@@ -636,6 +679,7 @@ khy_status khy_batch_autotune(khy_batch *b, int trial_steps, int *variant, float
         if (e == cudaSuccess && ms < best_ms) {
             best_ms = ms;
             best = v;
+            best_cps = cps;
         }
         // restore the state for the next trial
         if (e == cudaSuccess)
@@ -651,11 +695,10 @@ khy_status khy_batch_autotune(khy_batch *b, int trial_steps, int *variant, float
     b->wmin_valid = false;
     if (st != KHY_OK) return st;
     KHY_BCUDA(e);
-    if ((st = apply_variant(b, best)) != KHY_OK) return st;
-    (void)v0;
+    if ((st = apply_schedule(b, best, best_cps)) != KHY_OK) return st;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[std::make_tuple(b->ndim, b->prec, b->ngrids, b->cells)] = best;
+        g_tune_cache[shape_class(b)] = std::make_pair(best, best_cps);
     }
     if (variant) *variant = best;
     if (ms_per_step) *ms_per_step = best_ms;

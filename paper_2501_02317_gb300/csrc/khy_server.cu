@@ -39,6 +39,7 @@ using namespace khy;
 namespace {
 
 constexpr int kStepsPerIteration = 4;
+constexpr int kServeCtasPerSlot = 16;  // schedule pieces per resident CTA slot (khy_batch.cu)
 
 khy_status sfail(int st, const char *msg) { return (khy_status)record_error(st, msg); }
 
@@ -234,7 +235,9 @@ cudaError_t reschedule(khy_server *s, int nd) {
     s->nactive[nd] = (int)slots.size();
     std::vector<Geom> geoms;
     for (int k : slots) geoms.push_back(s->h_grids[k].g);
-    if (!slots.empty()) build_segments(slots, geoms, nd, tx, ty, std::max(1, resident), segs, cta);
+    // pieces of equal estimated cost, kServeCtasPerSlot per resident CTA
+    // slot (the hardware balances them, as in a batch)
+    if (!slots.empty()) build_segments(slots, geoms, nd, tx, ty, kServeCtasPerSlot * std::max(1, resident), segs, cta);
     else cta.assign(1, 0);
     s->nblocks[nd] = (int)cta.size() - 1;
     cudaError_t e = ensure_cap(&s->d_segs[nd], &s->cap_segs[nd], segs.size());

@@ -42,6 +42,7 @@ EXPORTS = [
     "khy_batch_create", "khy_batch_destroy", "khy_batch_set_primitive", "khy_batch_set_conserved",
     "khy_batch_get_conserved", "khy_batch_set_target", "khy_batch_enqueue_steps", "khy_batch_run",
     "khy_batch_get_clock", "khy_batch_autotune", "khy_batch_set_variant", "khy_batch_profile_steps",
+    "khy_batch_set_schedule", "khy_batch_get_schedule",
     "khy_batch_info", "khy_server_create", "khy_server_destroy", "khy_server_submit", "khy_server_poll",
     "khy_server_wait", "khy_server_result", "khy_server_stats",
 ]
@@ -130,6 +131,8 @@ def lib() -> ctypes.CDLL:
         "khy_batch_get_clock": [vp, i, P(d), P(l), P(d)],
         "khy_batch_autotune": [vp, i, P(i), P(ctypes.c_float)],
         "khy_batch_set_variant": [vp, i],
+        "khy_batch_set_schedule": [vp, i, i],
+        "khy_batch_get_schedule": [vp, P(i), P(i)],
         "khy_batch_profile_steps": [vp, l, P(ctypes.c_float)],
         "khy_batch_info": [vp, P(ctypes.c_longlong), P(st), P(i), P(i)],
         "khy_server_create": [st, i, vp, P(vp)],
@@ -437,6 +440,14 @@ class Batch:
 
     def set_variant(self, v: int) -> None:
         _check(lib().khy_batch_set_variant(self.h, int(v)))
+
+    def set_schedule(self, variant: int, ctas_per_slot: int) -> None:
+        _check(lib().khy_batch_set_schedule(self.h, int(variant), int(ctas_per_slot)))
+
+    def schedule(self) -> Tuple[int, int]:
+        v, c = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().khy_batch_get_schedule(self.h, ctypes.byref(v), ctypes.byref(c)))
+        return v.value, c.value
 
     def profile_steps(self, nsteps: int) -> Tuple[float, float, float]:
         ms = (ctypes.c_float * 3)()

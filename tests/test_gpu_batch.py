@@ -47,6 +47,29 @@ def test_batch_equals_alone_every_variant(kh, prec):
                 assert b.clock(k)[1] == 15
 
 
+@pytest.mark.parametrize("prec", [wl.PREC_MIXED, wl.PREC_FP64])
+def test_batch_schedules_equal_alone(kh, prec):
+    # the schedule (CTAs per resident slot) cuts the same tile runs into
+    # different pieces: every grid keeps the bits of the grid run alone
+    grids = blast_set(10, 7, prec)
+    meshes = [m for m, _ in grids]
+    alone = [gpu_run(m, W, max_steps=12)[0] for m, W in grids]
+    for v, cps in ((3, 1), (3, 4), (3, 32), (0, 16), (2, 256)):
+        with kh.Batch(meshes) as b:
+            b.set_schedule(v, cps)
+            assert b.schedule() == (v, cps)
+            b.set_primitive([W for _, W in grids])
+            b.set_target(1e30, 12)
+            b.run()
+            for k, U in enumerate(b.conserved()):
+                np.testing.assert_array_equal(U, alone[k])
+    with kh.Batch(meshes) as b:
+        with pytest.raises(kh.KhydroError):
+            b.set_schedule(3, 0)
+        with pytest.raises(kh.KhydroError):
+            b.set_schedule(7, 4)
+
+
 def test_batch_against_oracle(kh):
     grids = blast_set(5, 9, wl.PREC_MIXED)
     with kh.Batch([m for m, _ in grids]) as b:
@@ -66,7 +89,7 @@ def test_batch_per_grid_targets_and_autotune(kh):
     with kh.Batch(meshes) as b:
         b.set_primitive([W for _, W in grids])
         v, ms = b.autotune(2)          # must leave state and clocks untouched
-        assert 0 <= v < 5 and ms > 0
+        assert 0 <= v < 5 and ms > 0 and b.schedule()[0] == v and b.schedule()[1] in (1, 4, 16, 32)
         for k, te in enumerate(t_ends):
             b.set_target(te, -1, grid=k)
         b.run()
