@@ -364,11 +364,13 @@ def test_single_precision_conservation():
 # ------------------------------------------------------------ stored primitives vs on-the-fly recovery
 
 @pytest.mark.parametrize("prec", [wl.PREC_FP64, wl.PREC_MIXED, wl.PREC_FP32])
-@pytest.mark.parametrize("ndim", [1, 2, 3])
-def test_stored_primitives_match_lean_step_bitwise(prec, ndim):
+@pytest.mark.parametrize("ndim,n", [(1, (203, 1, 1)), (2, (70, 45, 1)), (3, (37, 19, 23)),
+                                    (2, (256, 41, 1)), (3, (68, 22, 19)), (3, (96, 16, 12))])
+def test_stored_primitives_match_lean_step_bitwise(prec, ndim, n):
     # the default Heun step reads stored primitives; the lean step recovers
-    # them from the state on the fly with the same function: same bits
-    n = {1: (203, 1, 1), 2: (70, 45, 1), 3: (37, 19, 23)}[ndim]
+    # them from the state on the fly with the same function: same bits.
+    # Full-width tiles with rows beyond the grid mapped by every boundary
+    # rule, tiles at grid edges and ragged tiles
     bc = ((wl.BC_REFLECT, wl.BC_OUTFLOW), (wl.BC_PERIODIC, wl.BC_PERIODIC), (wl.BC_FREE, wl.BC_REFLECT))
     mesh = wl.Mesh(ndim=ndim, n=n, gamma=1.4, cfl=0.3, prec=prec, bc=bc)
     W = wl.random_smooth(mesh, seed=11 + ndim)
