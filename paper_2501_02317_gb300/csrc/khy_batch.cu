@@ -60,15 +60,25 @@ __global__ void multi_wmin_reset_kernel(Clock *clocks, int ngrids) {
     if (i < ngrids) clocks[i].wmin_bits = kInfBits;
 }
 
-// a state between the host layout and the pool layout, one block per grid
+// a state between the host layout and the pool layout: blockIdx.x walks the
+// grids, blockIdx.y splits each grid's range (a batch of few large grids
+// still spreads over the GPU)
 __global__ void multi_relayout_kernel(const GridDesc *grids, const long long *hoff, int ngrids, int nvar,
                                       const double *src, double *dst, int to_pool) {
     for (int gi = blockIdx.x; gi < ngrids; gi += gridDim.x) {
         const long long n = (long long)nvar * grids[gi].g.ncell;
         const double *s = src + (to_pool ? hoff[gi] : grids[gi].off);
         double *d = dst + (to_pool ? grids[gi].off : hoff[gi]);
-        for (long long c = threadIdx.x; c < n; c += blockDim.x) d[c] = s[c];
+        for (long long c = threadIdx.x + (long long)blockIdx.y * blockDim.x; c < n; c += (long long)blockDim.x * gridDim.y)
+            d[c] = s[c];
     }
+}
+
+// launch shape of multi_relayout_kernel: about 2432 blocks in all
+dim3 relayout_grid(int ngrids) {
+    const int gx = std::min(ngrids, 2432);
+    const int gy = std::max(1, std::min(64, 2432 / std::max(1, ngrids)));
+    return dim3((unsigned)gx, (unsigned)gy, 1u);
 }
 
 // primitive (host layout: grids back to back, grid i at hoff[i]) ->
@@ -519,7 +529,7 @@ khy_status khy_batch_set_conserved(khy_batch *b, const double *U, size_t count) 
     if (!b || !U) return bfail(KHY_ERR_ARG, "khy_batch_set_conserved: NULL argument");
     if (count != b->hpool) return bfail(KHY_ERR_ARG, "khy_batch_set_conserved: count must be the sum of nvar*ncell");
     KHY_BCUDA(cudaMemcpyAsync(b->U1, U, sizeof(double) * count, cudaMemcpyHostToDevice, b->stream));  // staging
-    multi_relayout_kernel<<<std::min(b->ngrids, 152 * 8), 256, 0, b->stream>>>(b->d_grids, b->d_hoff, b->ngrids,
+    multi_relayout_kernel<<<relayout_grid(b->ngrids), 256, 0, b->stream>>>(b->d_grids, b->d_hoff, b->ngrids,
                                                                                 b->nvar, b->U1, b->U, 1);
     KHY_BCUDA(cudaGetLastError());
     KHY_BCUDA(cudaStreamSynchronize(b->stream));
@@ -531,7 +541,7 @@ khy_status khy_batch_get_conserved(khy_batch *b, double *U, size_t count) {
     if (!b || !U) return bfail(KHY_ERR_ARG, "khy_batch_get_conserved: NULL argument");
     if (count != b->hpool) return bfail(KHY_ERR_ARG, "khy_batch_get_conserved: count must be the sum of nvar*ncell");
     // U1 holds nothing between steps: it stages the host layout
-    multi_relayout_kernel<<<std::min(b->ngrids, 152 * 8), 256, 0, b->stream>>>(b->d_grids, b->d_hoff, b->ngrids,
+    multi_relayout_kernel<<<relayout_grid(b->ngrids), 256, 0, b->stream>>>(b->d_grids, b->d_hoff, b->ngrids,
                                                                                 b->nvar, b->U, b->U1, 0);
     KHY_BCUDA(cudaGetLastError());
     KHY_BCUDA(cudaMemcpyAsync(U, b->U1, sizeof(double) * count, cudaMemcpyDeviceToHost, b->stream));
