@@ -13,11 +13,12 @@
 //     is exact (Sterbenz); the density, velocities and the pressure leave it
 //     as FP32 primitives.
 //   * Flux differences: per cell and field, the six FP32 face fluxes are
-//     summed error-free as a float-float pair (Knuth TwoSum), the pair is
-//     turned into one double with integer operations, and the FP64 update
-//     costs one fused multiply-add per field (U + c S, or the Heun average
-//     V + (c/2) S from the stored V = (Un + U1)/2); each face flux still
-//     enters its two cells with opposite signs to full FP64 precision.
+//     summed error-free as a float-float pair (Knuth TwoSum); the first
+//     stage turns the pair into one double with integer operations and a
+//     scaled conversion of lo, and costs one fused multiply-add per field
+//     (U + c S); the Heun average adds the pair's two exact doubles to the
+//     stored V = (Un + U1)/2 with two; each face flux still enters its two
+//     cells with opposite signs to full FP64 precision.
 //   * The CFL minimum for the next step is taken in FP32 from the recovered
 //     primitives of the new state.
 //
@@ -61,26 +62,21 @@ __device__ __forceinline__ double f2d_fast(float x) {
 }
 
 // hi + lo of a float-float pair (|lo| <= ulp(hi)/2, as TwoSum and its
-// renormalisation produce) as one double, with integer operations only:
-// lo's significand is shifted into the 29 low significand bits that the
-// double of hi leaves zero and added (same sign) or subtracted (opposite
-// sign; from an exact power of two the result drops a binade, where the
-// unit halves).  Exact when the exponents differ by at most 29, otherwise
-// truncated below 2^-52 relative; a subnormal lo is dropped.  Replaces an
-// FP64 add in the update.
+// renormalisation produce) as one double: lo is scaled by a power of two
+// into units of the last place of the double of hi (the scale carries hi's
+// sign, so the count is signed relative to hi's magnitude), rounded to an
+// integer (exact when the exponents differ by at most 29, otherwise the
+// nearest unit: the sum rounded below 2^-52 relative) and added to the
+// double's bits; from an exact power of two a negative count drops a binade,
+// where the unit halves.  For |hi| below 2^-75 (the scale would leave FP32's
+// range) lo is dropped.  Replaces an FP64 add in the update.
 __device__ __forceinline__ double ff_to_double(float hi, float lo) {
-    const unsigned H = __float_as_uint(hi), L = __float_as_uint(lo);
-    const unsigned el = (L >> 23) & 0xFFu;
-    // exponent gap d - 24 (>= 0 for a normalised pair; hi = 0 wraps to a
-    // large shift): lo's 24-bit significand moved up 5 bits, then down by
-    // d - 24, sits d - 29 bits below the 29-bit boundary -- one shift either way
-    const unsigned k = min(((H >> 23) & 0xFFu) - el - 24u, 31u);
-    unsigned lp = (((L & 0x7FFFFFu) | 0x800000u) << 5) >> k;
-    if (el == 0u) lp = 0u;  // lo zero (or subnormal)
-    const bool same = ((H ^ L) & 0x80000000u) == 0u;
-    if (!same && (H & 0x7FFFFFu) == 0u) lp <<= 1;
-    const long long b = __double_as_longlong(f2d_fast(hi));
-    return __longlong_as_double(same ? b + (long long)lp : b - (long long)lp);
+    const unsigned H = __float_as_uint(hi);
+    // scale 2^(52 - e) with e hi's unbiased exponent: biased 306 - eh, at most 254
+    const unsigned es = min(306u - ((H >> 23) & 0xFFu), 254u);
+    int m = __float2int_rn(__fmul_rn(lo, __uint_as_float((es << 23) | (H & 0x80000000u))));
+    if ((H & 0x7FFFFFu) == 0u && m < 0) m += m;
+    return __longlong_as_double(__double_as_longlong(f2d_fast(hi)) + (long long)m);
 }
 
 // x / 2 by decrementing the exponent with integer operations: exact for

@@ -57,6 +57,18 @@ __device__ __forceinline__ FF2 ff_add2(FF2 a, FF2 b) {
     const float2 hi = add2(s.hi, e);
     return {hi, sub2(e, sub2(hi, s.hi))};
 }
+// a + b + c of three exact pairs as hi + lo without the renormalisation
+// (|lo| stays within a few units of hi's last place): the leading parts are
+// summed by two TwoSums and every error term is collected in lo -- for an
+// FP64 update that adds the two parts as separate doubles.
+__device__ __forceinline__ FF2 ff_sum3_unnorm(FF2 a, FF2 b, FF2 c) {
+    const FF2 t = two_sum2(a.hi, b.hi), u = two_sum2(t.hi, c.hi);
+    return {u.hi, add2(add2(add2(a.lo, b.lo), add2(c.lo, t.lo)), u.lo)};
+}
+__device__ __forceinline__ FF2 ff_sum2_unnorm(FF2 a, FF2 b) {
+    const FF2 t = two_sum2(a.hi, b.hi);
+    return {t.hi, add2(add2(a.lo, b.lo), t.lo)};
+}
 
 // a clamped to [lo, hi] per lane: with lo = min(b, 0), hi = max(b, 0) this is
 // minmod(a, b) of Eq. 3 (the value of the smaller magnitude when a and b share

@@ -555,13 +555,25 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                 for (int p = 0; p < (NV + 1) / 2; ++p) {
                     const float2 xl = pread(fxs, T::NXF, p, ix), xh = pread(fxs, T::NXF, p, ix + 1);
                     pk::FF2 Fs = pk::two_diff2(xl, xh);
-                    if (ND == 3) {
-                        const float2 yl = pread(fys, T::NYF, p, iy), yh = pread(fys, T::NYF, p, iy + TX);
-                        Fs = pk::ff_add2(Fs, pk::two_diff2(yl, yh));
-                    }
-                    if (ND >= 2) {
+                    if constexpr (HEUN2 && ND >= 2) {
+                        // the Heun average adds hi and lo as two doubles, so the
+                        // pair needs no renormalisation
                         const float2 ml = pread(fml, NT, p, tid), mh = pread(fmh, NT, p, tid);
-                        Fs = pk::ff_add2(Fs, pk::two_diff2(ml, mh));
+                        if constexpr (ND == 3) {
+                            const float2 yl = pread(fys, T::NYF, p, iy), yh = pread(fys, T::NYF, p, iy + TX);
+                            Fs = pk::ff_sum3_unnorm(Fs, pk::two_diff2(yl, yh), pk::two_diff2(ml, mh));
+                        } else {
+                            Fs = pk::ff_sum2_unnorm(Fs, pk::two_diff2(ml, mh));
+                        }
+                    } else {
+                        if (ND == 3) {
+                            const float2 yl = pread(fys, T::NYF, p, iy), yh = pread(fys, T::NYF, p, iy + TX);
+                            Fs = pk::ff_add2(Fs, pk::two_diff2(yl, yh));
+                        }
+                        if (ND >= 2) {
+                            const float2 ml = pread(fml, NT, p, tid), mh = pread(fmh, NT, p, tid);
+                            Fs = pk::ff_add2(Fs, pk::two_diff2(ml, mh));
+                        }
                     }
 #pragma unroll
                     for (int l = 0; l < 2; ++l) {
@@ -572,10 +584,10 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
                         double r;
                         if constexpr (HEUN2) {
                             // Heun average: V + (dt/2)(S_hi + S_lo) as two FP64
-                            // FMAs with the exact doubles of the pair (this
-                            // stage has FP64 issue to spare and its integer
-                            // pipe is the busier one; measured -1.8 % here,
-                            // +0.5 % in stage 1)
+                            // FMAs with the exact doubles of the pair, which
+                            // need not be renormalised (this stage has FP64
+                            // issue to spare; in stage 1, whose FP64 pipe also
+                            // forms V, the same form is 2 % slower)
                             const double v = FROM_V ? u : mx::half_exact(u);  // V, or (Un + U1)/2
                             r = __fma_rn(hcd, mx::f2d_fast(fhi), __fma_rn(hcd, mx::f2d_fast(flo), v));
                         } else {
