@@ -303,6 +303,10 @@ __device__ __forceinline__ void run_segment(const Geom &g, const S *__restrict__
             int actm = 0;
             if (ND >= 2) bc_map(L, g.n[DM], g.bc[DM][0], g.bc[DM][1], &actm);
             if (!x_rules && !y_rules && actm == 0) return;  // no ghost cell with a velocity rule
+            // (a CTA-uniform condition) every thread has waited for its own copies;
+            // the row copies of interior tiles assign elements to threads other than
+            // this loop does, so all of them must have landed before any is fixed
+            __syncthreads();
             R *dst = sW + (size_t)slot * NV * PC;
             for (int e = tid; e < PC; e += NTH) {
                 const int hx = e % PX, hy = e / PX;
