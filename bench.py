@@ -69,6 +69,10 @@ def _recorded_traffic(workload: str):
         return None
 
 
+# GB300 HBM3e nominal bandwidth (GB/s), the second denominator of the roofline
+NOMINAL_HBM_GBS = 7900.0
+
+
 def _sm_max_mhz() -> float:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -388,7 +392,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--side", "--n", dest="n", type=int, default=256, help="side of the 3D turbulence box")
@@ -454,6 +458,9 @@ def main():
     ms = sim.profile_steps(T_END, 5)
     stage_ms = ms[1] + ms[2]
     achieved = BYTES_PER_CELL_UPDATE_3D * ncell / (stage_ms * 1e-3) / 1e9
+    # DRAM bytes of the stage pair from the committed ncu capture (None when
+    # the stage kernels' sources changed since)
+    traffic = _recorded_traffic("turbulence-3d-%d^3-mixed" % args.n)
 
     # ---------------------------------------------------------- all-FP64 path
     fp64 = None
@@ -553,7 +560,9 @@ def main():
             "parity_256": parity,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                          "frac": achieved / peak_gbs,
-                         "traffic": _recorded_traffic("turbulence-3d-%d^3-mixed" % args.n),
+                         "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                         "traffic": traffic,
+                         "traffic_gbs": traffic / (stage_ms * 1e-3) / 1e9 if traffic else None,
                          "algorithmic_bytes": BYTES_PER_CELL_UPDATE_3D * ncell,
                          "kernel": "stage_kernel (stage 1 + stage 2 of one Heun step)",
                          "bytes_per_cell_update": BYTES_PER_CELL_UPDATE_3D, "stage_ms": [ms[1], ms[2]],
