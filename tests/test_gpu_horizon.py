@@ -9,7 +9,9 @@
   flux-difference accumulation keep the totals to machine accuracy).
 * 2D Kelvin-Helmholtz 1024^2 to t = 0.05 (the prefix of the t = 1 run on
   which the mixed gate is stated; later the shear layer's instability
-  amplifies rounding differences without bound).
+  amplifies rounding differences without bound), and the mixed path's
+  error curve against the all-FP64 path over the whole run to t = 1,
+  logged as data.
 * The 4096-grid blast batch (sides log-uniform in [32, 256]) stepped 200
   times in one launch per stage with the autotuned tile variant: a seeded
   sample of 64 grids against the oracle.
@@ -141,6 +143,40 @@ def test_kelvin_helmholtz_1024_to_t005(lib, kh1024_oracle, prec):
     errs = check_fields(mesh, U, Uo, prec == wl.PREC_FP64)
     _log("kh1024_t005_%s" % ("fp64" if prec == wl.PREC_FP64 else "mixed"),
          {"t": KH_T, "steps": s, "oracle_steps": so, "rel_l1": errs})
+
+
+# ------------------------------------------------------------ 2D Kelvin-Helmholtz 1024^2: error curve to t = 1
+
+KH_CURVE_T = (0.05, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0)
+
+
+def test_kelvin_helmholtz_1024_error_curve_to_t1(lib):
+    """The config's whole run, t = 0 .. 1: the mixed path against the
+    all-FP64 path (the oracle's step bit for bit, as the t = 0.05 test
+    shows; the oracle itself would take minutes on the host cores) at a
+    series of times.  Reported as data, gated only at t = 0.05: from there
+    the shear layer's instability amplifies rounding differences (Sec. 4.2
+    shows mixed and FP64 runs of a chaotic flow drifting apart the same
+    way).  Both runs must stay physical and land on every time exactly."""
+    from hydro_util import field_errors
+    mesh64, W = wl.kelvin_helmholtz(1024, prec=wl.PREC_FP64)
+    meshm, _ = wl.kelvin_helmholtz(1024, prec=wl.PREC_MIXED)
+    curve = []
+    with lib.Sim(mesh64) as s64, lib.Sim(meshm) as sm:
+        s64.set_primitive(W)
+        sm.set_primitive(W)
+        for tk in KH_CURVE_T:
+            _, t64 = s64.step_to(tk)
+            _, tm = sm.step_to(tk)
+            assert t64 == tk and tm == tk
+            U64 = s64.conserved()
+            Um = sm.conserved()
+            curve.append({"t": tk, "steps_fp64": s64.time()[1], "steps_mixed": sm.time()[1],
+                          "rel_l1": field_errors(meshm, Um, U64), "gate_errors": gate_errors(meshm, Um, U64)})
+        assert s64.flags() == (0, 0) and sm.flags() == (0, 0)
+    first = curve[0]
+    assert all(e <= g for e, g in zip(first["gate_errors"], mixed_gates(meshm.nvar))), first
+    _log("kh1024_error_curve_to_t1", {"fields": ["rho", "m_x", "m_y", "E", "p"], "curve": curve})
 
 
 # ------------------------------------------------------------ 4096-grid batch, 64-grid sample
