@@ -155,9 +155,10 @@ def test_kelvin_helmholtz_1024_error_curve_to_t1(lib):
     all-FP64 path (the oracle's step bit for bit, as the t = 0.05 test
     shows; the oracle itself would take minutes on the host cores) at a
     series of times.  Reported as data, gated only at t = 0.05: from there
-    the shear layer's instability amplifies rounding differences (Sec. 4.2
-    shows mixed and FP64 runs of a chaotic flow drifting apart the same
-    way).  Both runs must stay physical and land on every time exactly."""
+    the shear layer's instability amplifies rounding differences (the
+    paper's own mixed-against-FP64 comparison, the double Mach reflection of
+    Sec. 4.3, differs by up to about 1e-2 in density).  Both runs must stay
+    physical and land on every time exactly."""
     from hydro_util import field_errors
     mesh64, W = wl.kelvin_helmholtz(1024, prec=wl.PREC_FP64)
     meshm, _ = wl.kelvin_helmholtz(1024, prec=wl.PREC_MIXED)
