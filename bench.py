@@ -73,6 +73,35 @@ def _recorded_traffic(workload: str):
 NOMINAL_HBM_GBS = 7900.0
 
 
+def _recorded_warp_inst(workload: str):
+    """Warp instructions the stage-kernel pair executes per step, from the
+    committed ncu capture, or None when the sources changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "stage_traffic.json")) as f:
+            rec = json.load(f)
+        if rec.get("stage_sources_sha256") != stage_sources_sha256() or rec.get("workload") != workload:
+            return None
+        return float(rec["stage1_warp_inst"]) + float(rec["stage2_warp_inst"])
+    except Exception:
+        return None
+
+
+def issue_roofline(stage_ms: float, ncell: int, workload: str, sms: int, sm_mhz: float):
+    """The resource that bounds the mixed stage pair: instruction issue.
+    Executed warp instructions of the pair (ncu count) over its event-timed
+    duration, against one warp instruction per clock per SM sub-partition
+    (4 per SM) at the maximum SM clock.  Executed, not algorithmic,
+    instructions: this shows how close the kernel runs to its issue limit."""
+    inst = _recorded_warp_inst(workload)
+    peak = 4.0 * sms * sm_mhz * 1e6
+    if inst is None:
+        return {"bound": "issue", "achieved": None, "peak": peak, "unit": "warp-inst/s", "frac": None}
+    ach = inst / (stage_ms * 1e-3)
+    return {"bound": "issue", "achieved": ach, "peak": peak, "unit": "warp-inst/s", "frac": ach / peak,
+            "thread_inst_per_cell_update": inst * 32.0 / ncell,
+            "note": "executed instructions (ncu count of the committed capture), 4 warp-instructions per clock per SM"}
+
+
 def _sm_max_mhz() -> float:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -567,6 +596,9 @@ def main():
                          "kernel": "stage_kernel (stage 1 + stage 2 of one Heun step)",
                          "bytes_per_cell_update": BYTES_PER_CELL_UPDATE_3D, "stage_ms": [ms[1], ms[2]],
                          "clock_ms": ms[0], "peak_kind": peak_kind},
+            "issue_roofline": issue_roofline(stage_ms, ncell, "turbulence-3d-%d^3-mixed" % args.n,
+                                             torch.cuda.get_device_properties(local).multi_processor_count,
+                                             _sm_max_mhz()),
             "cpu_baseline": cpu,
             "batch": batch,
             "serving": serving,
