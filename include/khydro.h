@@ -238,7 +238,7 @@ khy_status khy_batch_run(khy_batch *b, long *batch_steps);
 khy_status khy_batch_get_clock(khy_batch *b, int grid, double *t, long *steps, double *dt);
 
 /* Autotuner: times every schedule -- tile variant x CTAs per resident CTA
- * slot in {1, 4, 16, 32} -- for trial_steps steps on the current state
+ * slot in {0 (queue), 1, 4, 16, 32} -- for trial_steps steps on the current state
  * (state and clocks are restored afterwards), keeps the fastest and
  * remembers it for batches of the same shape class (ndim, prec, grid count
  * and cell-weighted mean grid side, each to a power of two); new batches of
@@ -249,7 +249,9 @@ khy_status khy_batch_autotune(khy_batch *b, int trial_steps, int *variant, float
 /* Selects a schedule explicitly: tile variant (as khy_batch_set_variant)
  * and ctas_per_slot in [1, 256], the number of equal-cost pieces the tile
  * runs are cut into per resident CTA slot (default 16: more pieces than
- * slots, which the hardware balances).  Results do not depend on the
+ * slots, which the hardware balances), or 0: one persistent CTA per
+ * resident slot, each taking whole tile runs (cut only where the batch has
+ * too few) from a counter, longest first.  Results do not depend on the
  * schedule.  Errors: KHY_ERR_ARG. */
 khy_status khy_batch_set_schedule(khy_batch *b, int variant, int ctas_per_slot);
 

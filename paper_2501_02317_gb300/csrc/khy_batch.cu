@@ -40,9 +40,10 @@ namespace {
 
 constexpr int kBatchStepsPerGraph = 8;
 
-__global__ void multi_clock_kernel(const GridDesc *grids, Clock *clocks, int ngrids) {
+__global__ void multi_clock_kernel(const GridDesc *grids, Clock *clocks, int ngrids, int *queue) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < ngrids) clock_step(clocks + i, grids[i].g);
+    if (queue != nullptr && i < 2) queue[i] = 0;  // segment counters of the step's two stage launches
 }
 
 __global__ void multi_target_kernel(Clock *clocks, int first, int count, double t_end, long long max_steps) {
@@ -115,7 +116,9 @@ struct Schedule {
     int nblocks = 0;
 };
 
-Schedule build_schedule(const std::vector<GridDesc> &gd, int ndim, int TX, int TY, int resident) {
+// nblocks > 0: that many CTAs, each with its own contiguous share of the
+// segments; nblocks = 0: the queue schedule for `resident` persistent CTAs
+Schedule build_schedule(const std::vector<GridDesc> &gd, int ndim, int TX, int TY, int nblocks, int resident) {
     std::vector<int> ids(gd.size());
     std::vector<Geom> geoms(gd.size());
     for (size_t i = 0; i < gd.size(); ++i) {
@@ -123,7 +126,8 @@ Schedule build_schedule(const std::vector<GridDesc> &gd, int ndim, int TX, int T
         geoms[i] = gd[i].g;
     }
     Schedule s;
-    build_segments(ids, geoms, ndim, TX, TY, resident, s.segs, s.cta_seg);
+    if (nblocks > 0) build_segments(ids, geoms, ndim, TX, TY, nblocks, s.segs, s.cta_seg);
+    else build_segments_queue(ids, geoms, ndim, TX, TY, resident, s.segs, s.cta_seg);
     s.nblocks = (int)s.cta_seg.size() - 1;
     return s;
 }
@@ -134,8 +138,12 @@ Schedule build_schedule(const std::vector<GridDesc> &gd, int ndim, int TX, int T
 // slower one (the cost model ignores the small grids' fixed overheads).
 // 4096-grid 2D batch, mixed, tile rows of 124, cell-updates/s: 1 -> 1.24e10,
 // 4 -> 1.32e10, 8 -> 1.38e10, 16 -> 1.44e10, 32 -> 1.45e10, 64 -> 1.33e10.
+// ctas_per_slot = 0 is the queue schedule: one persistent CTA per resident
+// slot, each taking the next tile run (cut only where the batch has too few
+// of them) from a counter, longest first -- each run pays its warm-up
+// planes once instead of once per piece.
 constexpr int kDefaultCtasPerSlot = 16;
-constexpr int kTunedCtasPerSlot[] = {1, 4, 16, 32};
+constexpr int kTunedCtasPerSlot[] = {0, 1, 4, 16, 32};
 
 // Tuned (variant, ctas per slot) per batch shape class: dimensionality,
 // precision, log2 of the grid count and log2 of the cell-weighted mean grid
@@ -163,7 +171,9 @@ struct khy_batch {
     Clock *h_clocks = nullptr;  // pinned
     SegDesc *d_segs = nullptr;
     int *d_cta = nullptr;
+    int *d_queue = nullptr;  // segment counters of the queue schedule (one per stage launch)
     int nblocks = 0;
+    int nseg = 0;
     int variant = -1;
     int ctas_per_slot = kDefaultCtasPerSlot;
     cudaGraphExec_t graph = nullptr;
@@ -188,6 +198,8 @@ MultiArgs args_of(const khy_batch *b, int stage) {
     a.segs = b->d_segs;
     a.cta_seg = b->d_cta;
     a.clocks = b->d_clocks;
+    a.queue = b->ctas_per_slot == 0 ? b->d_queue + (stage - 1) : nullptr;
+    a.nseg = b->nseg;
     if (stage == 1) {
         a.Uin = b->U;
         a.Ubase = b->U;
@@ -217,10 +229,10 @@ khy_status apply_schedule(khy_batch *b, int v, int ctas_per_slot) {
     int tx = 0, ty = 0;
     multi_variant_tile(b->ndim, v, &tx, &ty);
     if (tx == 0) return bfail(KHY_ERR_ARG, "khy_batch: no such tile variant");
-    if (ctas_per_slot < 1 || ctas_per_slot > 256) return bfail(KHY_ERR_ARG, "khy_batch: ctas_per_slot must be in [1, 256]");
+    if (ctas_per_slot < 0 || ctas_per_slot > 256) return bfail(KHY_ERR_ARG, "khy_batch: ctas_per_slot must be in [0, 256]");
     const int resident = multi_resident(b->prec == KHY_PREC_FP64, b->ndim, v);
     if (resident <= 0) return bfail(KHY_ERR_CUDA, "khy_batch: kernel occupancy query failed");
-    Schedule s = build_schedule(b->gd, b->ndim, tx, ty, ctas_per_slot * resident);
+    Schedule s = build_schedule(b->gd, b->ndim, tx, ty, ctas_per_slot * resident, resident);
     cudaFree(b->d_segs);
     cudaFree(b->d_cta);
     b->d_segs = nullptr;
@@ -233,6 +245,7 @@ khy_status apply_schedule(khy_batch *b, int v, int ctas_per_slot) {
                               b->stream));
     KHY_BCUDA(cudaStreamSynchronize(b->stream));
     b->nblocks = s.nblocks;
+    b->nseg = (int)s.segs.size();
     b->variant = v;
     b->ctas_per_slot = ctas_per_slot;
     if (b->graph) {
@@ -243,7 +256,7 @@ khy_status apply_schedule(khy_batch *b, int v, int ctas_per_slot) {
 }
 
 cudaError_t enqueue_batch_step(const khy_batch *b) {
-    multi_clock_kernel<<<(b->ngrids + 127) / 128, 128, 0, b->stream>>>(b->d_grids, b->d_clocks, b->ngrids);
+    multi_clock_kernel<<<(b->ngrids + 127) / 128, 128, 0, b->stream>>>(b->d_grids, b->d_clocks, b->ngrids, b->d_queue);
     cudaError_t e = cudaGetLastError();
     const bool fp64 = b->prec == KHY_PREC_FP64;
     if (e == cudaSuccess) e = launch_multi_stage(fp64, args_of(b, 1), b->ndim, b->variant, 1, b->nblocks, b->stream);
@@ -377,6 +390,55 @@ void build_segments(const std::vector<int> &ids, const std::vector<Geom> &geoms,
     while (cta_seg.size() > 2 && cta_seg[cta_seg.size() - 2] == cta_seg.back()) cta_seg.pop_back();
 }
 
+// Queue schedule (persistent CTAs that take segments from a counter): every
+// tile run whole, cut into near-equal pieces only where it costs more than
+// 1/(4 resident) of the batch (at least 16 planes each), the list ordered
+// longest first; cta_seg splits it into min(resident, segments) contiguous
+// groups for the kernels that keep a static split (the CFL-minimum kernel).
+void build_segments_queue(const std::vector<int> &ids, const std::vector<Geom> &geoms, int ndim, int TX, int TY,
+                          int resident, std::vector<SegDesc> &segs, std::vector<int> &cta_seg) {
+    struct Piece { SegDesc s; double cost; };
+    const double fixed = 0.25 * TX * TY;
+    const double warm = ndim >= 2 ? 1.0 : 0.0;
+    std::vector<Piece> pieces;
+    double W = 0.0;
+    for (size_t i = 0; i < geoms.size(); ++i) {
+        const Geom &g = geoms[i];
+        const int nm = ndim >= 2 ? g.n[ndim - 1] : 1;
+        const int nty = ndim == 3 ? (g.n[1] + TY - 1) / TY : 1;
+        const int ntx = (g.n[0] + TX - 1) / TX;
+        for (int b = 0; b < nty; ++b)
+            for (int a = 0; a < ntx; ++a) {
+                const int w = std::min(TX, g.n[0] - a * TX);
+                const int h = ndim == 3 ? std::min(TY, g.n[1] - b * TY) : 1;
+                const double per = (double)w * h + fixed;
+                pieces.push_back(Piece{SegDesc{ids[i], a * TX, b * TY, 0, nm}, per});
+                W += per * (nm + warm);
+            }
+    }
+    const double cap = W / (4.0 * std::max(1, resident));
+    std::vector<Piece> cut;
+    for (const Piece &r : pieces) {
+        const int nm = r.s.k1;
+        const double full = (warm + nm) * r.cost;
+        int np = 1;
+        if (ndim >= 2 && full > cap) np = std::max(1, std::min((int)std::ceil(full / cap), nm / 16));
+        for (int q = 0; q < np; ++q) {
+            const int k0 = (int)((long long)nm * q / np), k1 = (int)((long long)nm * (q + 1) / np);
+            SegDesc sd = r.s;
+            sd.k0 = k0;
+            sd.k1 = k1;
+            cut.push_back(Piece{sd, (warm + (k1 - k0)) * r.cost});
+        }
+    }
+    std::stable_sort(cut.begin(), cut.end(), [](const Piece &a, const Piece &b) { return a.cost > b.cost; });
+    segs.clear();
+    for (const Piece &p : cut) segs.push_back(p.s);
+    const int G = std::max(1, std::min<int>(resident, (int)segs.size()));
+    cta_seg.assign(G + 1, 0);
+    for (int c = 0; c <= G; ++c) cta_seg[c] = (int)((long long)segs.size() * c / G);
+}
+
 void multi_variant_tile(int ndim, int variant, int *tx, int *ty) {
     // the same shapes as variant_tile() of the kernels (tx = 0: none)
     static const int table[4][kMultiVariants][2] = {{{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
@@ -457,6 +519,8 @@ khy_status khy_batch_create(const khy_mesh_desc *descs, int ngrids, void *cuda_s
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_hoff, b->hoff.data(), sizeof(long long) * ngrids, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_clocks, sizeof(Clock) * ngrids);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int), b->stream);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_clocks, sizeof(Clock) * ngrids);
     if (e == cudaSuccess) {
         for (int i = 0; i < ngrids; ++i) {
@@ -504,6 +568,7 @@ void khy_batch_destroy(khy_batch *b) {
     cudaFree(b->d_clocks);
     cudaFree(b->d_segs);
     cudaFree(b->d_cta);
+    cudaFree(b->d_queue);
     cudaFreeHost(b->h_clocks);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -625,7 +690,7 @@ khy_status khy_batch_profile_steps(khy_batch *b, long nsteps, float ms[3]) {
     for (long i = 0; i < nsteps && e == cudaSuccess; ++i) {
         e = cudaEventRecord(ev[0], b->stream);
         if (e == cudaSuccess) {
-            multi_clock_kernel<<<(b->ngrids + 127) / 128, 128, 0, b->stream>>>(b->d_grids, b->d_clocks, b->ngrids);
+            multi_clock_kernel<<<(b->ngrids + 127) / 128, 128, 0, b->stream>>>(b->d_grids, b->d_clocks, b->ngrids, b->d_queue);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);

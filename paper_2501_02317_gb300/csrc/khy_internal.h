@@ -48,6 +48,8 @@ int multi_resident_mixed(int ndim, int variant);
 // axis; the runs are cut at nblocks equal shares of the estimated cost.
 void build_segments(const std::vector<int> &ids, const std::vector<Geom> &geoms, int ndim, int TX, int TY,
                     int nblocks, std::vector<SegDesc> &segs, std::vector<int> &cta_seg);
+void build_segments_queue(const std::vector<int> &ids, const std::vector<Geom> &geoms, int ndim, int TX, int TY,
+                          int resident, std::vector<SegDesc> &segs, std::vector<int> &cta_seg);
 
 // Sets the shared-memory limits of the stage kernels of one dimensionality
 // and caches their persistent grid sizes; call before the first launch (in

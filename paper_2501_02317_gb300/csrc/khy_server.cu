@@ -191,6 +191,8 @@ MultiArgs srv_args(const khy_server *s, int nd, int stage) {
     a.segs = s->d_segs[nd];
     a.cta_seg = s->d_cta[nd];
     a.clocks = s->d_clocks;
+    a.queue = nullptr;
+    a.nseg = 0;
     double *U = s->arena, *U1 = s->arena + s->half;
     float *W0 = reinterpret_cast<float *>(s->arena + 2 * s->half), *W1 = W0 + s->half;
     if (stage == 1) {

@@ -939,6 +939,9 @@ struct MultiArgs {
     const void *Win;     // primitive pool the fluxes come from (W0 or W1, flux precision)
     void *Wout;          // primitive pool written (W1 or W0)
     Clock *clocks;       // one per grid
+    int *queue;          // non-null: persistent CTAs take segments 0 .. nseg - 1 in order from
+                         // this counter (zeroed before the launch) instead of cta_seg
+    int nseg;
 };
 
 template <class R, int ND, int STAGE, int TX, int TY>
@@ -950,11 +953,10 @@ __global__ void __launch_bounds__(cta_threads<R, ND, TX, TY>(), MinBlocks<R, cta
     R *sW = reinterpret_cast<R *>(smem_raw);
     R *sFx = sW + T::OFF_FX;
     R *sFy = sW + T::OFF_FY;
-    const int sb = a.cta_seg[blockIdx.x], se = a.cta_seg[blockIdx.x + 1];
-    for (int si = sb; si < se; ++si) {
+    auto run_one = [&](int si) {
         const SegDesc sd = a.segs[si];
         Clock *clk = a.clocks + sd.grid;
-        if (!clk->active) continue;  // same value for every thread of the CTA
+        if (!clk->active) return;  // same value for every thread of the CTA
         const GridDesc *gd = a.grids + sd.grid;
         const Geom g = gd->g;
         const double dtdx[3] = {clk->dtdx[0], clk->dtdx[1], clk->dtdx[2]};
@@ -965,7 +967,23 @@ __global__ void __launch_bounds__(cta_threads<R, ND, TX, TY>(), MinBlocks<R, cta
                                           reinterpret_cast<R *>(a.Wout) + gd->off, dtdx, gd->cubic,
                                           sd.x0, sd.y0, sd.k0, sd.k1, sW, sFx, sFy, flags, floors, wmin);
         reduce_to_clock<STAGE, NTH>(clk, flags, floors, wmin);
+    };
+    if (a.queue != nullptr) {
+        // persistent CTA: the next segment from the shared counter (segments
+        // are ordered longest first, so the last ones to start are short)
+        __shared__ int s_next;
+        for (;;) {
+            __syncthreads();  // every thread has read the previous s_next
+            if (threadIdx.x == 0) s_next = atomicAdd(a.queue, 1);
+            __syncthreads();
+            const int si = s_next;
+            if (si >= a.nseg) break;
+            run_one(si);
+        }
+        return;
     }
+    const int sb = a.cta_seg[blockIdx.x], se = a.cta_seg[blockIdx.x + 1];
+    for (int si = sb; si < se; ++si) run_one(si);
 }
 
 // Per-grid CFL minimum of every grid over the same segments (after the

@@ -54,7 +54,7 @@ def test_batch_schedules_equal_alone(kh, prec):
     grids = blast_set(10, 7, prec)
     meshes = [m for m, _ in grids]
     alone = [gpu_run(m, W, max_steps=12)[0] for m, W in grids]
-    for v, cps in ((3, 1), (3, 4), (3, 32), (0, 16), (2, 256)):
+    for v, cps in ((3, 1), (3, 4), (3, 32), (0, 16), (2, 256), (3, 0), (0, 0)):
         with kh.Batch(meshes) as b:
             b.set_schedule(v, cps)
             assert b.schedule() == (v, cps)
@@ -65,7 +65,9 @@ def test_batch_schedules_equal_alone(kh, prec):
                 np.testing.assert_array_equal(U, alone[k])
     with kh.Batch(meshes) as b:
         with pytest.raises(kh.KhydroError):
-            b.set_schedule(3, 0)
+            b.set_schedule(3, -1)
+        with pytest.raises(kh.KhydroError):
+            b.set_schedule(3, 257)
         with pytest.raises(kh.KhydroError):
             b.set_schedule(7, 4)
 
@@ -89,7 +91,7 @@ def test_batch_per_grid_targets_and_autotune(kh):
     with kh.Batch(meshes) as b:
         b.set_primitive([W for _, W in grids])
         v, ms = b.autotune(2)          # must leave state and clocks untouched
-        assert 0 <= v < 5 and ms > 0 and b.schedule()[0] == v and b.schedule()[1] in (1, 4, 16, 32)
+        assert 0 <= v < 5 and ms > 0 and b.schedule()[0] == v and b.schedule()[1] in (0, 1, 4, 16, 32)
         for k, te in enumerate(t_ends):
             b.set_target(te, -1, grid=k)
         b.run()
