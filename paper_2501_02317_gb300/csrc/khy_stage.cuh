@@ -29,10 +29,13 @@
 // fly one, so stages 5, 6 give the same bits as stages 1, 2.
 //
 // Work decomposition.  The grid is cut into tiles of TX x TY columns along
-// the slowest ("march") axis -- z in 3D, y in 2D; a 1D grid is one row.  The
-// launch is persistent: one CTA per resident slot, and CTA b owns the b-th
-// equal share of the (tile, plane) sequence, so every SM gets the same number
-// of planes.  A CTA walks each of its tile segments plane by plane: a plane
+// the slowest ("march") axis -- z in 3D, y in 2D; a 1D grid is one row.  On
+// large grids every tile column is cut at the same plane boundaries into
+// runs (StageArgs::kb), one CTA per run, numbered chunk-major, so CTAs that
+// run at the same time hold neighbouring tiles at the same planes and share
+// their halo rows through L2; smaller grids use a persistent launch, one CTA
+// per resident slot, CTA b owning the b-th equal share of the (tile, plane)
+// sequence.  A CTA walks each of its tile segments plane by plane: a plane
 // of primitives with a two-cell halo on every side -- copied from the stored
 // primitives (cp.async, one plane ahead) or recovered from the state (Sec.
 // 3.1) -- with the ghost-zone rules applied by index mapping (Sec. 3.1.1) is
@@ -840,8 +843,8 @@ __device__ __forceinline__ void reduce_to_clock(Clock *clk, unsigned flags, unsi
 }
 
 // Mixed path: cap registers at 64 per thread so that 1024 threads per SM stay
-// resident (two 512-thread CTAs); the all-FP64 path is limited by shared
-// memory instead.
+// resident (four 256-thread CTAs of a 3D tile); the all-FP64 path is limited
+// by shared memory instead.
 template <class R, int NT>  // NT: threads per CTA
 struct MinBlocks {
     static constexpr int value = std::is_same<R, float>::value ? (1024 / NT > 0 ? 1024 / NT : 1) : 1;
