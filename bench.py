@@ -312,7 +312,7 @@ def bench_batch(khydro, wl, torch, steps: int = 200):
             "variant": variant, "ctas_per_slot": ctas_per_slot, "ctas": info["nblocks"], "launches_per_step": 3, "all_grids_stepped": done}
 
 
-def bench_serving(khydro, wl, njobs: int = 1000, budget_bytes: int = 16 << 30, slots: int = 64):
+def bench_serving(khydro, wl, njobs: int = 2000, budget_bytes: int = 16 << 30, slots: int = 64):
     """Serving: the first `njobs` jobs of the seeded Poisson stream (mean 200
     jobs/s; 2D 64^2-512^2 and 3D 32^3-128^3, KH / blast / turbulence, t_end
     U[0.05, 0.5]) submitted at their arrival times; then the same jobs as
@@ -320,6 +320,23 @@ def bench_serving(khydro, wl, njobs: int = 1000, budget_bytes: int = 16 << 30, s
     (the stream's exponential inter-arrival times rescaled to the lower rate).
     Time-to-solution = finish - submit."""
     jobs = wl.serving_stream(njobs, seed=4)
+    # the initial states are generated before the clock starts (submissions
+    # keep to the arrival times): keep them within half the host memory
+    # available, else serve the longest prefix of the stream that fits
+    ic_bytes = [(j.ndim + 2) * j.side ** j.ndim * 8 for j in jobs]
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        avail = None
+    note = None
+    if avail is not None and 2 * sum(ic_bytes) > avail:
+        keep, acc = 0, 0
+        while keep < len(jobs) and 2 * (acc + ic_bytes[keep]) <= avail:
+            acc += ic_bytes[keep]
+            keep += 1
+        note = "first %d of %d jobs: their initial states fill half the %.0f GB of free host memory" % (
+            keep, njobs, avail / 1e9)
+        jobs = jobs[:keep]
     ics = [wl.job_initial_state(j) for j in jobs]
 
     def run(arrivals, offered):
@@ -349,8 +366,10 @@ def bench_serving(khydro, wl, njobs: int = 1000, budget_bytes: int = 16 << 30, s
     sat = run(base, rate0)
     cap = sat["achieved_jobs_per_s"]  # jobs/s the server sustained while saturated
     out = {"workload": "Poisson 200 jobs/s (seed 4), first %d jobs, mixed, HBM budget %d GiB, %d slots"
-                       % (njobs, budget_bytes >> 30, slots),
+                       % (len(jobs), budget_bytes >> 30, slots),
            "offered_200_per_s": sat, "capacity_jobs_per_s": cap}
+    if note:
+        out["note"] = note
     for frac in (0.5, 0.9):
         rate = frac * cap
         arr = [a * rate0 / rate for a in base]  # the same exponential gaps, mean 1/rate
@@ -436,7 +455,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the FP64, FP32, van Leer and lean-Heun legs (headline only)")
-    ap.add_argument("--serve-jobs", type=int, default=1000, help="jobs of the serving stream")
+    ap.add_argument("--serve-jobs", type=int, default=2000, help="jobs of the serving stream")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
