@@ -282,10 +282,17 @@ def parity_against_oracle(khydro, wl, mesh0, W, Uo, steps: int):
     return out
 
 
-def bench_batch(khydro, wl, torch, steps: int = 200):
+# 2D Heun cell-update: stage 1 reads Un, writes U1; stage 2 reads U1 and Un,
+# writes Un+1 (four fields of 8 B each)
+BYTES_PER_CELL_UPDATE_2D = 160
+
+
+def bench_batch(khydro, wl, torch, steps: int = 200, peak_gbs: float = None):
     """Batched workload: 4096 independent 2D blast grids (sides log-uniform in
     [32, 256], seed 3), mixed precision, one launch per stage for all grids,
-    tile variant picked by the autotuner; `steps` Heun steps of every grid."""
+    tile variant picked by the autotuner; `steps` Heun steps of every grid.
+    The HBM fraction divides the algorithmic bytes by the whole step (clock
+    launch included), a lower bound on the stage kernels' own fraction."""
     grids = wl.batch_blasts(4096)
     meshes = [m for m, _ in grids]
     cells = sum(m.ncell for m in meshes)
@@ -309,7 +316,10 @@ def bench_batch(khydro, wl, torch, steps: int = 200):
         done = all(b.clock(k)[1] == steps + 3 for k in (0, len(meshes) // 2, len(meshes) - 1))
     return {"workload": "4096 2D blast grids, sides log-U[32,256] (seed 3), mixed, periodic", "grids": len(meshes),
             "cells": cells, "steps": steps, "value": cells * steps / el, "unit": UNIT, "ms_per_step": 1e3 * el / steps,
-            "variant": variant, "ctas_per_slot": ctas_per_slot, "ctas": info["nblocks"], "launches_per_step": 3, "all_grids_stepped": done}
+            "variant": variant, "ctas_per_slot": ctas_per_slot, "ctas": info["nblocks"], "launches_per_step": 3, "all_grids_stepped": done,
+            "bytes_per_cell_update": BYTES_PER_CELL_UPDATE_2D,
+            "hbm_achieved_gbs": BYTES_PER_CELL_UPDATE_2D * cells * steps / el / 1e9,
+            "hbm_frac": (BYTES_PER_CELL_UPDATE_2D * cells * steps / el / 1e9 / peak_gbs) if peak_gbs else None}
 
 
 def bench_serving(khydro, wl, njobs: int = 2000, budget_bytes: int = 16 << 30, slots: int = 64):
@@ -620,7 +630,7 @@ def main():
             s.close()
     sim.close()
 
-    batch = None if args.no_batch or world > 1 else bench_batch(khydro, wl, torch)
+    batch = None if args.no_batch or world > 1 else bench_batch(khydro, wl, torch, peak_gbs=peak_gbs)
     serving = None if args.no_serve or world > 1 else bench_serving(khydro, wl, njobs=args.serve_jobs)
 
     cpu = None
