@@ -599,12 +599,17 @@ def main():
             bufs.append(Uh)
         torch.cuda.synchronize()
 
+        errors = []
+
         def pipeline(i, nsteps):
-            torch.cuda.set_device(local)
-            for _ in range(nsteps):
-                sims_e2e[i].set_conserved(bufs[i])
-                sims_e2e[i].enqueue_steps(T_END, 1)
-                sims_e2e[i].conserved(bufs[i])
+            try:
+                torch.cuda.set_device(local)
+                for _ in range(nsteps):
+                    sims_e2e[i].set_conserved(bufs[i])
+                    sims_e2e[i].enqueue_steps(T_END, 1)
+                    sims_e2e[i].conserved(bufs[i])
+            except Exception as e:  # re-raised on the main thread: no number from a failed pipeline
+                errors.append(e)
 
         def run_e2e(npipe):
             barrier()
@@ -616,6 +621,8 @@ def main():
             for t in th:
                 t.join()
             torch.cuda.synchronize()
+            if errors:
+                raise errors[0]
             return max_over_ranks(time.perf_counter() - t0)
 
         el1 = run_e2e(1)
