@@ -13,6 +13,7 @@ import tempfile
 import pytest
 
 import oracle
+from paper_2501_02317_gb300 import workloads as wl
 import test_oracle_pins as pins
 import test_oracle_vl2_pins as vpins
 
@@ -38,6 +39,16 @@ MUTANTS = {
                           "double ke = rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);"),
     "transverse_slot": ("int t2 = d == 2 ? 1 : 2;", "int t2 = d == 2 ? 0 : 2;"),
     "outflow_clamp_direction": ("if (side == 0) { if (*vn > 0.0) *vn = 0.0; }", "if (side == 0) { if (*vn < 0.0) *vn = 0.0; }"),
+    "outflow_high_clamp_direction": ("else { if (*vn < 0.0) *vn = 0.0; }", "else { if (*vn > 0.0) *vn = 0.0; }"),
+    "zero_gradient_from_second_cell": ("else src = side == 0 ? 0 : n - 1; /* free, outflow */",
+                                       "else src = side == 0 ? 1 : n - 2; /* free, outflow */"),
+    "reflect_mirror_about_centre": ("else if (bc == ORC_BC_REFLECT) src = side == 0 ? g - 1 : n - g;",
+                                    "else if (bc == ORC_BC_REFLECT) src = side == 0 ? g : n - 1 - g;"),
+    "dt_not_clipped_to_t_end": ("    double rem = t_end - *t;\n    if (dt >= rem) { dt = rem; last = 1; }\n    double *dU = (double *)malloc(sizeof(double) * (size_t)NV);\n    double *U1",
+                                "    double rem = t_end - *t;\n    if (0 && dt >= rem) { dt = rem; last = 1; }\n    double *dU = (double *)malloc(sizeof(double) * (size_t)NV);\n    double *U1"),
+    "cfl_constant_dropped": ("return m->cfl * wmin;", "return wmin;"),
+    "dtdx_wrong_axis": ("const double dtdx = dt / cell_width(m, d);", "const double dtdx = dt / cell_width(m, 0);"),
+    "heun_corrector_from_old_state": ("orc_rhs(m, U1, dt, dU, flags);", "orc_rhs(m, U, dt, dU, flags);"),
     "q_no_sqrt": ("double ql = sqrt(1.0 + g1 * (ratl - 1.0));", "double ql = (1.0 + g1 * (ratl - 1.0));"),
     "flux_diff_sign": ("dU[uc] = dU[uc] - dtdx * dif[0];", "dU[uc] = dU[uc] + dtdx * dif[0];"),
     "two_shock_sign": ("pstar = (gl * pl + gr * pr - (ur - ul)) / (gl + gr);", "pstar = (gl * pl + gr * pr + (ur - ul)) / (gl + gr);"),
@@ -70,6 +81,8 @@ PIN_CHECKS = [
     pins.test_outflow_momentum_budget,
     pins.test_reflecting_walls_conserve_mass_and_energy,
     pins.test_outflow_does_not_inflow,
+    pins.test_outflow_refuses_inflow_on_both_sides,
+    lambda: [pins.test_zero_gradient_ends_carry_the_edge_cells_physical_flux(b) for b in (wl.BC_FREE, wl.BC_OUTFLOW)],
     pins.test_implosion_diagonal_symmetry,
     pins.test_sod_against_exact_solution,
     lambda: pins.test_sound_wave_second_order(5.0 / 3.0, 1e-6),

@@ -312,6 +312,49 @@ def test_outflow_does_not_inflow():
     assert U[0, 0, 0, 0] < U0[0, 0, 0, 0]
 
 
+def test_outflow_refuses_inflow_on_both_sides():
+    # the same uniform flow entering through the high end instead: the mirror
+    # image (x -> 1 - x, v -> -v) of the low-side case must give the mirrored
+    # state, the high-side ghost clamping the normal velocity to point out
+    m = wl.Mesh(ndim=1, n=(32, 1, 1), gamma=1.4, cfl=0.4, bc=((wl.BC_OUTFLOW, wl.BC_OUTFLOW),) * 3)
+    Wa = wl.uniform(m, rho=1.0, v=(0.5, 0, 0), p=1.0)
+    Wb = wl.uniform(m, rho=1.0, v=(-0.5, 0, 0), p=1.0)
+    Ua, ta, sa, _ = oracle.run(m, oracle.prim_to_cons(m, Wa), 0.0, 0.05)
+    Ub, tb, sb, _ = oracle.run(m, oracle.prim_to_cons(m, Wb), 0.0, 0.05)
+    assert sa == sb and ta == tb
+    mirror = Ua[:, :, :, ::-1] * np.array([1.0, -1.0, 1.0])[:, None, None, None]
+    np.testing.assert_allclose(Ub, mirror, rtol=1e-13, atol=1e-13)
+    assert Ub[0, 0, 0, -1] < 1.0  # the refused inflow thins the gas at the high end
+
+
+@pytest.mark.parametrize("bc", [wl.BC_FREE, wl.BC_OUTFLOW])
+def test_zero_gradient_ends_carry_the_edge_cells_physical_flux(bc):
+    # free ends, and outflow ends whose normal velocity already points out,
+    # copy the edge cell into both ghost layers (Sec. 3.1.1): the minmod
+    # slopes at the boundary face vanish, both face states are the edge
+    # cell's, and HLLC of two equal states is the physical flux of Eq. 2.  So
+    # one right-hand side changes the totals by the two edge cells' physical
+    # fluxes alone: sum_i dU_i = -(dt/dx) (F(W_last) - F(W_first))
+    n, g = 48, 1.4
+    m = wl.Mesh(ndim=1, n=(n, 1, 1), gamma=g, cfl=0.4, bc=((bc, bc),) * 3)
+    x = (np.arange(n) + 0.5) / n
+    W = np.zeros(m.shape)
+    W[0, 0, 0] = 1.0 + 0.2 * np.sin(2.0 * np.pi * x)
+    W[1, 0, 0] = 0.6 * (x - 0.5)  # points out of the domain at both ends
+    W[2, 0, 0] = 1.0 + 0.1 * np.cos(2.0 * np.pi * x)
+    dt = 1e-3
+    dU, f = oracle.rhs(m, oracle.prim_to_cons(m, W), dt)
+    assert f == 0
+
+    def flux(r, u, p):  # Euler flux of Eq. 2, 1D
+        E = p / (g - 1.0) + 0.5 * r * u * u
+        return np.array([r * u, r * u * u + p, (E + p) * u])
+
+    want = -(dt * n) * (flux(*W[:, 0, 0, -1]) - flux(*W[:, 0, 0, 0]))
+    got = dU.reshape(3, -1).sum(axis=1)
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-14)
+
+
 def test_implosion_diagonal_symmetry():
     # Sec. 4.4: the implosion is symmetric about the diagonal x = y; the
     # unsplit update keeps that symmetry to the last bit
