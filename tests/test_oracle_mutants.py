@@ -49,6 +49,15 @@ MUTANTS = {
     "cfl_constant_dropped": ("return m->cfl * wmin;", "return wmin;"),
     "dtdx_wrong_axis": ("const double dtdx = dt / cell_width(m, d);", "const double dtdx = dt / cell_width(m, 0);"),
     "heun_corrector_from_old_state": ("orc_rhs(m, U1, dt, dU, flags);", "orc_rhs(m, U, dt, dU, flags);"),
+    # primitive floors and status flags (Sec. 3.1 recovery)
+    "p_floor_dropped": ("if (p < m->p_floor) { p = m->p_floor; *flags |= ORC_FLAG_FLOOR; }",
+                        "if (0) { p = m->p_floor; *flags |= ORC_FLAG_FLOOR; }"),
+    "rho_floor_after_velocity": (
+        "    if (rho < m->rho_floor) { rho = m->rho_floor; *flags |= ORC_FLAG_FLOOR; }\n"
+        "    double v[3] = {0.0, 0.0, 0.0};\n    for (int d = 0; d < nd; ++d) v[d] = u[1 + d] / rho;",
+        "    double v[3] = {0.0, 0.0, 0.0};\n    for (int d = 0; d < nd; ++d) v[d] = u[1 + d] / rho;\n"
+        "    if (rho < m->rho_floor) { rho = m->rho_floor; *flags |= ORC_FLAG_FLOOR; }"),
+    "negative_eint_not_flagged": ("if (!(eint >= 0.0)) *flags |= ORC_FLAG_NONPHYSICAL;", "if (0) *flags |= ORC_FLAG_NONPHYSICAL;"),
     "q_no_sqrt": ("double ql = sqrt(1.0 + g1 * (ratl - 1.0));", "double ql = (1.0 + g1 * (ratl - 1.0));"),
     "flux_diff_sign": ("dU[uc] = dU[uc] - dtdx * dif[0];", "dU[uc] = dU[uc] + dtdx * dif[0];"),
     "two_shock_sign": ("pstar = (gl * pl + gr * pr - (ur - ul)) / (gl + gr);", "pstar = (gl * pl + gr * pr + (ur - ul)) / (gl + gr);"),
@@ -76,6 +85,8 @@ PIN_CHECKS = [
     pins.test_hllc_mirror_symmetry,
     pins.test_uniform_dt_closed_form,
     pins.test_prim_cons_roundtrip,
+    lambda: [pins.test_recovery_floors_and_flags(c) for c in
+             ("regular", "rho_below_floor", "negative_eint", "negative_rho")],
     lambda: [pins.test_uniform_state_stays_uniform(nd) for nd in (1, 2, 3)],
     lambda: [pins.test_conservation_periodic(nd) for nd in (1, 2, 3)],
     pins.test_outflow_momentum_budget,

@@ -312,6 +312,48 @@ def test_outflow_does_not_inflow():
     assert U[0, 0, 0, 0] < U0[0, 0, 0, 0]
 
 
+@pytest.mark.parametrize("case", ["regular", "rho_below_floor", "negative_eint", "negative_rho"])
+def test_recovery_floors_and_flags(case):
+    # floors act on the recovered primitive only (no floor in the paper; the
+    # reading recorded with the oracle): a density below the floor is raised
+    # to it and the momentum divided by the raised density; a pressure below
+    # its floor (a negative internal energy included) is raised to the floor;
+    # each raises the floor flag, and a non-positive density or a negative
+    # internal energy the non-physical flag.  Values from the definitions.
+    g = 1.4
+    m = wl.Mesh(ndim=1, n=(2, 1, 1), gamma=g, cfl=0.4, bc=((wl.BC_PERIODIC, wl.BC_PERIODIC),) * 3)
+    rf, pf = m.rho_floor, m.p_floor
+    u = {"regular": (1.0, 0.5, 2.0), "rho_below_floor": (0.25 * rf, 2.5e-11, 1.0),
+         "negative_eint": (1.0, 2.0, 1.0), "negative_rho": (-1.0, 0.0, 1.0)}[case]
+    U = np.zeros(m.shape)
+    U[:, 0, 0, :] = np.array(u)[:, None]
+    W, f = oracle.cons_to_prim(m, U)
+    rho, mom, E = u
+    if case == "regular":
+        want = (1.0, 0.5, (g - 1.0) * (2.0 - 0.5 * 0.25))
+        want_f = 0
+    elif case == "rho_below_floor":
+        v = mom / rf
+        want = (rf, v, (g - 1.0) * (E - 0.5 * rf * v * v))
+        want_f = oracle.FLAG_FLOOR
+    elif case == "negative_eint":  # ke = 2 > E = 1
+        want = (1.0, 2.0, pf)
+        want_f = oracle.FLAG_FLOOR | oracle.FLAG_NONPHYSICAL
+    else:  # the floored density is used to go on; the state is flagged
+        want = (rf, 0.0, (g - 1.0) * E)
+        want_f = oracle.FLAG_FLOOR | oracle.FLAG_NONPHYSICAL
+    np.testing.assert_allclose(W[:, 0, 0, 0], want, rtol=1e-15, atol=0.0)
+    np.testing.assert_array_equal(W[:, 0, 0, 0], W[:, 0, 0, 1])
+    assert f == want_f
+    if case == "rho_below_floor":
+        # the floor never writes back into the conserved state: a uniform
+        # state below the density floor has equal fluxes on every face, so a
+        # step leaves it unchanged to the bit
+        U2, _, _, f2 = oracle.heun_step(m, U, 0.0, 1e30)
+        np.testing.assert_array_equal(U2, U)
+        assert f2 == oracle.FLAG_FLOOR
+
+
 def test_outflow_refuses_inflow_on_both_sides():
     # the same uniform flow entering through the high end instead: the mirror
     # image (x -> 1 - x, v -> -v) of the low-side case must give the mirrored
