@@ -58,6 +58,10 @@ MUTANTS = {
         "    double v[3] = {0.0, 0.0, 0.0};\n    for (int d = 0; d < nd; ++d) v[d] = u[1 + d] / rho;\n"
         "    if (rho < m->rho_floor) { rho = m->rho_floor; *flags |= ORC_FLAG_FLOOR; }"),
     "negative_eint_not_flagged": ("if (!(eint >= 0.0)) *flags |= ORC_FLAG_NONPHYSICAL;", "if (0) *flags |= ORC_FLAG_NONPHYSICAL;"),
+    # compensated conservation totals
+    "totals_compensation_dropped": ("out[q] = s + comp;", "out[q] = s;"),
+    "totals_compensation_branch_swapped": ("if (fabs(s) >= fabs(x)) comp += (s - t) + x;",
+                                           "if (fabs(s) <= fabs(x)) comp += (s - t) + x;"),
     "q_no_sqrt": ("double ql = sqrt(1.0 + g1 * (ratl - 1.0));", "double ql = (1.0 + g1 * (ratl - 1.0));"),
     "flux_diff_sign": ("dU[uc] = dU[uc] - dtdx * dif[0];", "dU[uc] = dU[uc] + dtdx * dif[0];"),
     "two_shock_sign": ("pstar = (gl * pl + gr * pr - (ur - ul)) / (gl + gr);", "pstar = (gl * pl + gr * pr + (ur - ul)) / (gl + gr);"),
@@ -89,6 +93,7 @@ PIN_CHECKS = [
              ("regular", "rho_below_floor", "negative_eint", "negative_rho")],
     lambda: [pins.test_uniform_state_stays_uniform(nd) for nd in (1, 2, 3)],
     lambda: [pins.test_conservation_periodic(nd) for nd in (1, 2, 3)],
+    pins.test_totals_are_compensated_sums,
     pins.test_outflow_momentum_budget,
     pins.test_reflecting_walls_conserve_mass_and_energy,
     pins.test_outflow_does_not_inflow,

@@ -354,6 +354,32 @@ def test_recovery_floors_and_flags(case):
         assert f2 == oracle.FLAG_FLOOR
 
 
+def test_totals_are_compensated_sums():
+    # the conservation totals are compensated (Neumaier) sums: on fields whose
+    # large terms cancel, a plain left-to-right sum loses the small ones
+    # entirely, the compensated sum keeps them (reference: math.fsum, the
+    # exactly rounded sum)
+    import math
+    m = wl.Mesh(ndim=1, n=(1000, 1, 1), gamma=1.4, cfl=0.4, bc=((wl.BC_PERIODIC, wl.BC_PERIODIC),) * 3)
+    rng = np.random.default_rng(8)
+    U = np.empty(m.shape)
+    for q in range(m.nvar):
+        x = rng.uniform(0.5, 1.5, 1000)
+        big = np.arange(0, 900, 97)
+        x[big] = 1e17 * rng.uniform(1.0, 2.0, big.size)  # large terms ...
+        x[big + 50] = -x[big]                            # ... each cancelled 50 cells later
+        U[q, 0, 0] = x
+    tot = oracle.totals(m, U)
+    for q in range(m.nvar):
+        x = U[q].ravel()
+        exact = math.fsum(x)
+        plain = 0.0
+        for v in x:
+            plain += v
+        assert abs(plain - exact) > 1.0          # the inputs defeat a plain sum
+        assert abs(tot[q] - exact) <= 1e-9 * abs(exact)      # |exact| ~ 1e3
+
+
 def test_outflow_refuses_inflow_on_both_sides():
     # the same uniform flow entering through the high end instead: the mirror
     # image (x -> 1 - x, v -> -v) of the low-side case must give the mirrored
