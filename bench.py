@@ -322,6 +322,22 @@ def bench_batch(khydro, wl, torch, steps: int = 200, peak_gbs: float = None):
             "hbm_frac": (BYTES_PER_CELL_UPDATE_2D * cells * steps / el / 1e9 / peak_gbs) if peak_gbs else None}
 
 
+def serving_prefix(jobs, avail_bytes):
+    """How many jobs of the stream to serve: all of them when their FP64
+    initial states take at most half of `avail_bytes` of free host memory
+    (None: unknown, serve all), else the longest prefix that does.  Returns
+    (count, note or None)."""
+    ic_bytes = [(j.ndim + 2) * j.side ** j.ndim * 8 for j in jobs]
+    if avail_bytes is None or 2 * sum(ic_bytes) <= avail_bytes:
+        return len(jobs), None
+    keep, acc = 0, 0
+    while keep < len(jobs) and 2 * (acc + ic_bytes[keep]) <= avail_bytes:
+        acc += ic_bytes[keep]
+        keep += 1
+    return keep, "first %d of %d jobs: their initial states fill half the %.0f GB of free host memory" % (
+        keep, len(jobs), avail_bytes / 1e9)
+
+
 def bench_serving(khydro, wl, njobs: int = 2000, budget_bytes: int = 16 << 30, slots: int = 64):
     """Serving: the first `njobs` jobs of the seeded Poisson stream (mean 200
     jobs/s; 2D 64^2-512^2 and 3D 32^3-128^3, KH / blast / turbulence, t_end
@@ -333,20 +349,12 @@ def bench_serving(khydro, wl, njobs: int = 2000, budget_bytes: int = 16 << 30, s
     # the initial states are generated before the clock starts (submissions
     # keep to the arrival times): keep them within half the host memory
     # available, else serve the longest prefix of the stream that fits
-    ic_bytes = [(j.ndim + 2) * j.side ** j.ndim * 8 for j in jobs]
     try:
         avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
     except (ValueError, OSError):
         avail = None
-    note = None
-    if avail is not None and 2 * sum(ic_bytes) > avail:
-        keep, acc = 0, 0
-        while keep < len(jobs) and 2 * (acc + ic_bytes[keep]) <= avail:
-            acc += ic_bytes[keep]
-            keep += 1
-        note = "first %d of %d jobs: their initial states fill half the %.0f GB of free host memory" % (
-            keep, njobs, avail / 1e9)
-        jobs = jobs[:keep]
+    keep, note = serving_prefix(jobs, avail)
+    jobs = jobs[:keep]
     ics = [wl.job_initial_state(j) for j in jobs]
 
     def run(arrivals, offered):
