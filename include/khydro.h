@@ -113,6 +113,10 @@ typedef struct khy_sim khy_sim;
  * the device clock on the current CUDA device, and binds the stream
  * (cudaStream_t, may be NULL).
  * On success *out receives the simulation, time t = 0, state zero.
+ * A valid desc has ndim in 1..3, at least 2 cells on every active axis and
+ * n = 1 on the others, at most 2^31 cells in all, finite lo < hi on every
+ * active axis, gamma > 1, 0 < cfl <= 1, non-negative floors, and khy_bc,
+ * khy_prec and khy_integrator values in range.
  * Errors: KHY_ERR_ARG (invalid desc), KHY_ERR_OOM, KHY_ERR_CUDA. */
 khy_status khy_create(const khy_mesh_desc *desc, void *cuda_stream, khy_sim **out);
 

@@ -167,16 +167,18 @@ khy_status validate(const khy_mesh_desc *d) {
     for (int a = 0; a < 3; ++a) {
         if (a < d->ndim) {
             if (d->n[a] < 2) return fail(KHY_ERR_ARG, "n[%d] = %d: active axes need at least 2 cells", a, d->n[a]);
-            if (!(d->hi[a] > d->lo[a])) return fail(KHY_ERR_ARG, "hi[%d] must exceed lo[%d]", a, a);
+            if (!(d->hi[a] > d->lo[a]) || !std::isfinite(d->lo[a]) || !std::isfinite(d->hi[a]))
+                return fail(KHY_ERR_ARG, "hi[%d] must exceed lo[%d], both finite", a, a);
             for (int s = 0; s < 2; ++s)
                 if (d->bc[a][s] < KHY_BC_PERIODIC || d->bc[a][s] > KHY_BC_REFLECT)
                     return fail(KHY_ERR_ARG, "bc[%d][%d] = %d is not a khy_bc", a, s, d->bc[a][s]);
         } else if (d->n[a] != 1) {
             return fail(KHY_ERR_ARG, "n[%d] must be 1 for ndim = %d", a, d->ndim);
         }
+        // checked before the product can exceed 2^31 (and long long's range)
+        if (ncell > (1LL << 31) / d->n[a]) return fail(KHY_ERR_ARG, "too many cells (more than 2^31)");
         ncell *= d->n[a];
     }
-    if (ncell > (1LL << 31)) return fail(KHY_ERR_ARG, "too many cells (%lld > 2^31)", ncell);
     if (!(d->gamma > 1.0) || !std::isfinite(d->gamma)) return fail(KHY_ERR_ARG, "gamma must be > 1");
     if (!(d->cfl > 0.0 && d->cfl <= 1.0)) return fail(KHY_ERR_ARG, "cfl must be in (0, 1]");
     if (d->prec != KHY_PREC_FP64 && d->prec != KHY_PREC_MIXED && d->prec != KHY_PREC_FP32)

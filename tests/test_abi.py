@@ -62,6 +62,10 @@ def test_version(L):
     dict(hi=(0.0, 1.0, 1.0)),
     dict(bc=((9, 0), (0, 0), (0, 0))),
     dict(rho_floor=-1.0),
+    dict(ndim=3, n=(1 << 30, 1 << 30, 1 << 30)),   # the cell count's product would overflow
+    dict(ndim=2, n=(1 << 16, 1 << 16, 1)),         # 2^32 cells
+    dict(hi=(float("inf"), 1.0, 1.0)),
+    dict(lo=(float("nan"), 0.0, 0.0)),
 ])
 def test_create_rejects_invalid_descriptors(L, bad):
     base = dict(ndim=1, n=(8, 1, 1))
